@@ -1,0 +1,150 @@
+/*
+ * libksort: K-sort on one GB300 GPU (CUDA, sm_103a), behind a plain C ABI.
+ *
+ * K-sort (Sundararajan, Pal, Chakraborty, Mahanti, arxiv 1107.3622, Section 1.1) is
+ * the interchange-free Quick sort whose partition (Steps 1-4) takes the FIRST element
+ * of a sub-array as the key, sends every element x with key <= x to the right of the
+ * key and every other element to its left, and writes the key at its final index
+ * i = left + #{x < key}; Steps 5-6 then sort the two sides the same way.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers on the calling thread's current CUDA
+ *     device; they must be aligned to the key size. The caller owns them.
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream) and return
+ *     once the work is enqueued. Errors found on the host (bad pointer, size, dtype)
+ *     return at once and enqueue nothing.
+ *   - Errors found on the device (bad offsets, exhausted workspace, a wait that ran
+ *     past its time limit) set a flag that ksort_get_device_error() reads. No kernel
+ *     traps, asserts or spins without a bound.
+ *   - Each (device, stream) pair owns a private workspace (scratch keys, work queue,
+ *     look-back descriptors) that the library allocates on first use and grows as
+ *     needed. Calls on the same stream are ordered; calls on different streams use
+ *     different workspaces and may overlap. Growing a workspace is not allowed while
+ *     the stream is being captured into a CUDA graph: reserve it first with
+ *     ksort_reserve_workspace().
+ *   - Float keys compare with IEEE `<=` (Step 3). A NaN is never >= the key, so it goes
+ *     left; a NaN key sends every element left. +0 and -0 compare equal.
+ *   - A single sub-array may hold at most 2^31 - 1 keys.
+ */
+#ifndef KSORT_H
+#define KSORT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KSORT_API __attribute__((visibility("default")))
+#else
+#define KSORT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *ksort_stream_t;
+
+typedef enum { KSORT_F32 = 0, KSORT_F64 = 1, KSORT_U32 = 2 } ksort_dtype_t;
+
+typedef enum {
+    KSORT_OK = 0,
+    KSORT_ERR_INVALID_ARG = 1,        /* NULL/misaligned/host pointer, bad size       */
+    KSORT_ERR_UNSUPPORTED_DTYPE = 2,
+    KSORT_ERR_OUT_OF_MEMORY = 3,      /* workspace could not be allocated or grown    */
+    KSORT_ERR_CUDA = 4,               /* a CUDA runtime call failed                   */
+    KSORT_ERR_TIMEOUT = 5,            /* device: a bounded wait ran past its limit     */
+    KSORT_ERR_BAD_OFFSETS = 6,        /* device: offsets decrease, leave [0, total],
+                                         or one array exceeds 2^31 - 1 keys           */
+    KSORT_ERR_WORKSPACE_EXHAUSTED = 7,/* device: the work queue or look-back arena was
+                                         too small (adversarial, near-O(n^2) inputs)   */
+    KSORT_ERR_INTERNAL = 8
+} ksort_status_t;
+
+/* Steps 1-4 once, in place, on keys_dev[0..n-1] (Section 1.1, Steps 1-4).
+ * After the call keys[0..i) < key, keys[i] == key (the original keys[0]) and
+ * keys(i..n) >= key, with i = #{x in keys[1..n) : x < key}. The order inside each side
+ * is not the paper's (only the index and the two multisets are defined).
+ * *key_index_dev (device int64) receives i. n >= 1. */
+KSORT_API ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, int64_t n,
+                               int64_t *key_index_dev, ksort_stream_t stream);
+
+/* The same partition, out of place: in_dev is read, out_dev (n keys, not overlapping
+ * in_dev) receives the partitioned keys. One read and one write pass over the keys. */
+KSORT_API ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
+                                   int64_t n, int64_t *key_index_dev, ksort_stream_t stream);
+
+/* Steps 1-6: sorts keys_dev[0..n-1] ascending, in place (Section 1.1). The recursion of
+ * Steps 5-6 runs on the device (persistent kernel with a work queue); sub-arrays of at
+ * most the tuned cutoff are finished inside shared memory by the same key rule.
+ * n == 0 or 1 is a no-op. */
+KSORT_API ksort_status_t ksort_sort(ksort_dtype_t dtype, void *keys_dev, int64_t n, ksort_stream_t stream);
+
+/* Sorts num_arrays independent arrays in one launch: array r is
+ * keys_dev[offsets_dev[r] .. offsets_dev[r+1]). offsets_dev is a device int64 array of
+ * num_arrays + 1 nondecreasing entries within [0, total_keys]; total_keys bounds the
+ * keys touched (it sizes the scratch). Offsets are checked on the device
+ * (KSORT_ERR_BAD_OFFSETS). Capturable in a CUDA graph once the workspace is reserved. */
+KSORT_API ksort_status_t ksort_sort_batched(ksort_dtype_t dtype, void *keys_dev, const int64_t *offsets_dev,
+                                  int64_t num_arrays, int64_t total_keys, ksort_stream_t stream);
+
+/* Makes sure the workspace of (current device, stream) can serve sorts of up to
+ * max_total_keys keys of `dtype` in up to max_arrays arrays. Synchronises the stream
+ * if it has to grow the workspace. */
+KSORT_API ksort_status_t ksort_reserve_workspace(ksort_dtype_t dtype, int64_t max_total_keys,
+                                       int64_t max_arrays, ksort_stream_t stream);
+
+/* Frees the workspace of (current device, stream) after synchronising the stream. */
+KSORT_API ksort_status_t ksort_release_workspace(ksort_stream_t stream);
+
+/* Synchronises `stream`, then returns and clears the device error flag of its
+ * workspace (KSORT_OK if none). A CUDA error found while synchronising is returned
+ * as KSORT_ERR_CUDA. */
+KSORT_API ksort_status_t ksort_get_device_error(ksort_stream_t stream);
+
+/* Counters of the last ksort_sort / ksort_sort_batched on `stream` (synchronises). */
+typedef struct {
+    uint64_t large_items;   /* sub-arrays partitioned by multi-CTA tile passes        */
+    uint64_t large_keys;    /* keys in those sub-arrays (each read once, written once) */
+    uint64_t tiles;         /* tile passes run                                         */
+    uint64_t small_items;   /* sub-arrays finished in shared memory                    */
+    uint64_t small_keys;    /* keys in those sub-arrays                                */
+    uint64_t smem_levels;   /* partition levels run inside shared memory (all items)   */
+    uint64_t lookback_steps;/* 32-wide look-back windows examined                      */
+    uint64_t items_pushed;  /* work-queue entries used                                 */
+} ksort_stats_t;
+KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out);
+
+/* Tuning for one dtype (process-wide). Zero fields keep their current value.
+ *   cutoff:        sub-arrays with at most this many keys are finished in shared
+ *                  memory (2 .. ksort_max_cutoff(dtype));
+ *   ctas_per_sm:   persistent-kernel CTAs per SM (capped by occupancy);
+ *   spin_limit_ms: time limit of every device-side wait. */
+typedef struct {
+    int32_t cutoff;
+    int32_t ctas_per_sm;
+    int32_t spin_limit_ms;
+    int32_t reserved;
+} ksort_tuning_t;
+KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
+KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);
+KSORT_API int32_t ksort_max_cutoff(ksort_dtype_t dtype);
+
+/* Keys handled by one tile pass of the partition kernels for `dtype`. */
+KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
+
+/* Failure-path check: runs one device-side wait, of the kind the partition's look-back
+ * uses, on a flag that nothing ever sets. The wait gives up after limit_ms (1..60000),
+ * records KSORT_ERR_TIMEOUT in the stream's workspace and returns; the next
+ * ksort_get_device_error(stream) reports it. No fault, trap or endless loop. */
+KSORT_API ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stream);
+
+/* Static text for a status code. */
+KSORT_API const char *ksort_status_string(ksort_status_t status);
+
+/* Text of the last CUDA runtime error seen by this thread inside the library. */
+KSORT_API const char *ksort_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KSORT_H */

@@ -1,0 +1,262 @@
+"""K-sort on GB300: Python binding of libksort (include/ksort.h).
+
+K-sort (arxiv 1107.3622, Section 1.1) partitions a sub-array around its first element
+(Steps 1-4: x goes right of the key when key <= x) and recurses on both sides
+(Steps 5-6). Every step runs in the CUDA kernels of libksort.so; this module only
+marshals arguments (torch tensors -> device pointers, the current torch stream) and
+turns status codes into exceptions. PyTorch supplies device memory and streams.
+
+The functions named ``ksort_*`` mirror the C entry points one to one. The short
+helpers (``partition_``, ``sort_``, ``sort_batched_``) wrap them for tensors.
+There is no CPU fallback: without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "KSortError", "F32", "F64", "U32", "load", "library_path",
+    "ksort_partition", "ksort_partition_out", "ksort_sort", "ksort_sort_batched",
+    "ksort_reserve_workspace", "ksort_release_workspace", "ksort_get_device_error",
+    "ksort_get_stats", "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
+    "ksort_tile_keys", "ksort_status_string", "ksort_last_cuda_error",
+    "ksort_selftest_wait_timeout",
+    "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
+]
+
+F32, F64, U32 = 0, 1, 2
+_NAMES = {F32: "f32", F64: "f64", U32: "u32"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_lib", "libksort.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class KSortError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {ksort_status_string(status)} (status {status})"
+        if status == 4:
+            msg += f" [{ksort_last_cuda_error()}]"
+        super().__init__(msg)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "large_items", "large_keys", "tiles", "small_items", "small_keys",
+        "smem_levels", "lookback_steps", "items_pushed")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("cutoff", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("spin_limit_ms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Loads the in-tree libksort.so, building it first if it is missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import _build
+        if not _build.up_to_date():
+            try:
+                _build.build()
+            except Exception as e:  # no toolkit: fail loudly, never fall back
+                if not os.path.exists(_LIB_PATH):
+                    raise RuntimeError(
+                        f"libksort.so is not built and could not be built: {e}") from e
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        sig = {
+            "ksort_partition": (i32, [i32, vp, i64, vp, vp]),
+            "ksort_partition_out": (i32, [i32, vp, vp, i64, vp, vp]),
+            "ksort_sort": (i32, [i32, vp, i64, vp]),
+            "ksort_sort_batched": (i32, [i32, vp, vp, i64, i64, vp]),
+            "ksort_reserve_workspace": (i32, [i32, i64, i64, vp]),
+            "ksort_release_workspace": (i32, [vp]),
+            "ksort_get_device_error": (i32, [vp]),
+            "ksort_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+            "ksort_set_tuning": (i32, [i32, ctypes.POINTER(Tuning)]),
+            "ksort_get_tuning": (i32, [i32, ctypes.POINTER(Tuning)]),
+            "ksort_max_cutoff": (i32, [i32]),
+            "ksort_tile_keys": (i32, [i32]),
+            "ksort_status_string": (ctypes.c_char_p, [i32]),
+            "ksort_last_cuda_error": (ctypes.c_char_p, []),
+            "ksort_selftest_wait_timeout": (i32, [i32, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return _lib
+
+
+# ----------------------------------------------------------------------------- helpers
+def dtype_code(t, dtype=None) -> int:
+    """Key type code of a tensor. int32 tensors are taken as uint32 bit patterns only
+    when ``dtype='u32'`` is given."""
+    import torch
+    if dtype is not None:
+        code = {"f32": F32, "f64": F64, "u32": U32}[dtype]
+        want = {F32: (torch.float32,), F64: (torch.float64,),
+                U32: (torch.uint32, torch.int32)}[code]
+        if t.dtype not in want:
+            raise TypeError(f"tensor dtype {t.dtype} does not hold {dtype} keys")
+        return code
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.uint32:
+        return U32
+    raise TypeError(f"unsupported key dtype {t.dtype} (float32, float64, uint32)")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise KSortError(status, where)
+
+
+# ----------------------------------------------------------------------------- C names
+def ksort_partition(dtype: int, keys, n: int, key_index, stream=None):
+    _check(load().ksort_partition(dtype, _ptr(keys), n, _ptr(key_index), _stream(stream)),
+           "ksort_partition")
+
+
+def ksort_partition_out(dtype: int, src, dst, n: int, key_index, stream=None):
+    _check(load().ksort_partition_out(dtype, _ptr(src), _ptr(dst), n, _ptr(key_index),
+                                      _stream(stream)), "ksort_partition_out")
+
+
+def ksort_sort(dtype: int, keys, n: int, stream=None):
+    _check(load().ksort_sort(dtype, _ptr(keys), n, _stream(stream)), "ksort_sort")
+
+
+def ksort_sort_batched(dtype: int, keys, offsets, num_arrays: int, total_keys: int, stream=None):
+    _check(load().ksort_sort_batched(dtype, _ptr(keys), _ptr(offsets), num_arrays, total_keys,
+                                     _stream(stream)), "ksort_sort_batched")
+
+
+def ksort_reserve_workspace(dtype: int, max_total_keys: int, max_arrays: int = 1, stream=None):
+    _check(load().ksort_reserve_workspace(dtype, max_total_keys, max_arrays, _stream(stream)),
+           "ksort_reserve_workspace")
+
+
+def ksort_release_workspace(stream=None):
+    _check(load().ksort_release_workspace(_stream(stream)), "ksort_release_workspace")
+
+
+def ksort_get_device_error(stream=None) -> int:
+    """Synchronises the stream; returns (and clears) the device status code."""
+    return int(load().ksort_get_device_error(_stream(stream)))
+
+
+def ksort_get_stats(stream=None) -> dict:
+    s = Stats()
+    _check(load().ksort_get_stats(_stream(stream), ctypes.byref(s)), "ksort_get_stats")
+    return s.as_dict()
+
+
+def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0):
+    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, 0)
+    _check(load().ksort_set_tuning(dtype, ctypes.byref(t)), "ksort_set_tuning")
+
+
+def ksort_get_tuning(dtype: int) -> dict:
+    t = Tuning()
+    _check(load().ksort_get_tuning(dtype, ctypes.byref(t)), "ksort_get_tuning")
+    return {"cutoff": t.cutoff, "ctas_per_sm": t.ctas_per_sm, "spin_limit_ms": t.spin_limit_ms}
+
+
+def ksort_max_cutoff(dtype: int) -> int:
+    return int(load().ksort_max_cutoff(dtype))
+
+
+def ksort_tile_keys(dtype: int) -> int:
+    return int(load().ksort_tile_keys(dtype))
+
+
+def ksort_selftest_wait_timeout(limit_ms: int, stream=None):
+    _check(load().ksort_selftest_wait_timeout(limit_ms, _stream(stream)),
+           "ksort_selftest_wait_timeout")
+
+
+def ksort_status_string(status: int) -> str:
+    return load().ksort_status_string(status).decode()
+
+
+def ksort_last_cuda_error() -> str:
+    return load().ksort_last_cuda_error().decode()
+
+
+# ----------------------------------------------------------------------------- tensors
+def partition_(t, dtype=None, stream=None) -> int:
+    """Steps 1-4 in place on a 1-D CUDA tensor; returns the key's final index."""
+    import torch
+    code = dtype_code(t, dtype)
+    idx = torch.empty(1, dtype=torch.int64, device=t.device)
+    ksort_partition(code, t, t.numel(), idx, stream)
+    return int(idx.item())
+
+
+def partition_out(src, dst, dtype=None, stream=None):
+    """Steps 1-4 from ``src`` into ``dst``; returns the key index as a device tensor."""
+    import torch
+    code = dtype_code(src, dtype)
+    if dst.dtype != src.dtype or dst.numel() != src.numel():
+        raise ValueError("dst must match src in dtype and size")
+    idx = torch.empty(1, dtype=torch.int64, device=src.device)
+    ksort_partition_out(code, src, dst, src.numel(), idx, stream)
+    return idx
+
+
+def sort_(t, dtype=None, stream=None):
+    """Steps 1-6: sorts a 1-D CUDA tensor ascending, in place."""
+    ksort_sort(dtype_code(t, dtype), t, t.numel(), stream)
+    return t
+
+
+def sort_batched_(flat, offsets, dtype=None, stream=None):
+    """Sorts flat[offsets[r]:offsets[r+1]] for every r in one launch (int64 offsets
+    on the device)."""
+    import torch
+    if offsets.dtype != torch.int64 or not offsets.is_cuda:
+        raise ValueError("offsets must be a CUDA int64 tensor")
+    ksort_sort_batched(dtype_code(flat, dtype), flat, offsets, offsets.numel() - 1,
+                       flat.numel(), stream)
+    return flat

@@ -1,0 +1,500 @@
+// C ABI of libksort (include/ksort.h): argument checks, per-(device, stream)
+// workspaces, tuning, and dispatch to the per-key-type launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "../../include/ksort.h"
+#include "ksort_device.cuh"
+#include "ksort_internal.h"
+
+namespace ksort {
+namespace {
+
+thread_local char g_cuda_error[256] = "";
+
+ksort_status_t cuda_fail(cudaError_t e) {
+  std::snprintf(g_cuda_error, sizeof(g_cuda_error), "%s: %s", cudaGetErrorName(e),
+                cudaGetErrorString(e));
+  return KSORT_ERR_CUDA;
+}
+
+#define KS_CUDA(call)                          \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+size_t key_bytes(ksort_dtype_t dt) { return dt == KSORT_F64 ? 8 : 4; }
+bool dtype_ok(int dt) { return dt == KSORT_F32 || dt == KSORT_F64 || dt == KSORT_U32; }
+
+// ------------------------------------------------------------------ per-type dispatch
+struct Ops {
+  KernelInfo (*info)();
+  size_t (*sort_smem_bytes)(int);
+  cudaError_t (*max_ctas_per_sm)(int, int *);
+  cudaError_t (*partition_out)(const PartParams &, int, cudaStream_t);
+  cudaError_t (*seed)(const SortParams &, cudaStream_t);
+  cudaError_t (*sort)(const SortParams &, int, cudaStream_t);
+  long long (*tile_count)(const void *, long long, long long);
+};
+
+template <typename K>
+Ops ops_for() {
+  return Ops{&Launcher<K>::info,          &Launcher<K>::sort_smem_bytes,
+             &Launcher<K>::max_ctas_per_sm, &Launcher<K>::partition_out,
+             &Launcher<K>::seed,          &Launcher<K>::sort,
+             &Launcher<K>::tile_count};
+}
+
+const Ops &ops(ksort_dtype_t dt) {
+  static const Ops f32 = ops_for<float>(), f64 = ops_for<double>(), u32 = ops_for<unsigned>();
+  return dt == KSORT_F64 ? f64 : dt == KSORT_U32 ? u32 : f32;
+}
+
+// ------------------------------------------------------------------ tuning
+struct Tuning {
+  int cutoff;
+  int ctas_per_sm;  // 0: as many as fit
+  int spin_limit_ms;
+};
+
+std::mutex g_mu;
+Tuning g_tuning[3] = {{4096, 0, 2000}, {4096, 0, 2000}, {4096, 0, 2000}};
+
+// ------------------------------------------------------------------ workspaces
+struct Workspace {
+  void *base = nullptr;
+  size_t bytes = 0;
+  Control *ctl = nullptr;
+  PartCtl *pctl = nullptr;
+  unsigned long long *lb = nullptr;
+  unsigned long long lb_cap = 0;
+  Item *items = nullptr;
+  ItemCtl *ictl = nullptr;
+  unsigned long long item_cap = 0;
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  unsigned pending_error = 0;  // device error carried over from a replaced allocation
+};
+
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Need {
+  unsigned long long item_cap, lb_cap;
+  size_t scratch_bytes;
+};
+
+// Work-queue and look-back capacities. Up to 2^21 keys the queue can hold one entry
+// per key, which covers every input (a sort makes at most n - 1 partition calls);
+// beyond that it holds n/32 entries, ~100x what random inputs use. Inputs that need
+// more (near-O(n^2) orders) stop with KSORT_ERR_WORKSPACE_EXHAUSTED.
+Need need_for(ksort_dtype_t dt, long long total, long long arrays) {
+  const KernelInfo ki = ops(dt).info();
+  const unsigned long long t = (unsigned long long)std::max<long long>(total, 1);
+  const unsigned long long a = (unsigned long long)std::max<long long>(arrays, 1);
+  unsigned long long items = t <= (1ull << 21) ? t : std::max(1ull << 21, t / 32);
+  items += a + 64;
+  const unsigned long long tiles_per_level = (t + ki.tile_keys - 1) / ki.tile_keys + a + 1;
+  const unsigned long long lb = std::max(1ull << 21, 64ull * tiles_per_level);
+  return Need{items, lb, (size_t)t * key_bytes(dt)};
+}
+
+ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspace **out) {
+  Workspace &ws = g_ws[{dev, s}];
+  if (ws.base && ws.item_cap >= need.item_cap && ws.lb_cap >= need.lb_cap &&
+      ws.scratch_bytes >= need.scratch_bytes) {
+    *out = &ws;
+    return KSORT_OK;
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  KS_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return KSORT_ERR_OUT_OF_MEMORY;
+
+  const unsigned long long item_cap = std::max(need.item_cap, ws.item_cap);
+  const unsigned long long lb_cap = std::max(need.lb_cap, ws.lb_cap);
+  const size_t scratch_bytes = std::max(need.scratch_bytes, ws.scratch_bytes);
+
+  if (ws.base) {
+    KS_CUDA(cudaStreamSynchronize(s));
+    unsigned err = 0;
+    KS_CUDA(cudaMemcpy(&err, &ws.ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err && !ws.pending_error) ws.pending_error = err;
+    KS_CUDA(cudaFree(ws.base));
+    ws.base = nullptr;
+  }
+  // [Control][PartCtl][look-back][items][item counters][scratch keys]
+  size_t off = 0;
+  const size_t o_ctl = off;
+  off = align_up(off + sizeof(Control), 256);
+  const size_t o_pctl = off;
+  off += sizeof(PartCtl);  // look-back follows directly: one memset clears both
+  const size_t o_lb = off;
+  off = align_up(off + lb_cap * sizeof(unsigned long long), 256);
+  const size_t o_items = off;
+  off = align_up(off + item_cap * sizeof(Item), 256);
+  const size_t o_ictl = off;
+  off = align_up(off + item_cap * sizeof(ItemCtl), 256);
+  const size_t meta = off;
+  const size_t o_scr = off;
+  off = align_up(off + scratch_bytes, 256);
+
+  void *base = nullptr;
+  cudaError_t e = cudaMalloc(&base, off);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ws = Workspace{};
+    return KSORT_ERR_OUT_OF_MEMORY;
+  }
+  KS_CUDA(cudaMemsetAsync(base, 0, meta, s));
+  char *b = static_cast<char *>(base);
+  const unsigned pending = ws.pending_error;
+  ws = Workspace{};
+  ws.base = base;
+  ws.bytes = off;
+  ws.ctl = reinterpret_cast<Control *>(b + o_ctl);
+  ws.pctl = reinterpret_cast<PartCtl *>(b + o_pctl);
+  ws.lb = reinterpret_cast<unsigned long long *>(b + o_lb);
+  ws.lb_cap = lb_cap;
+  ws.items = reinterpret_cast<Item *>(b + o_items);
+  ws.ictl = reinterpret_cast<ItemCtl *>(b + o_ictl);
+  ws.item_cap = item_cap;
+  ws.scratch = b + o_scr;
+  ws.scratch_bytes = scratch_bytes;
+  ws.pending_error = pending;
+  *out = &ws;
+  return KSORT_OK;
+}
+
+ksort_status_t check_device_ptr(const void *p, size_t align, int dev) {
+  if (!p) return KSORT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(p) % align) return KSORT_ERR_INVALID_ARG;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return KSORT_ERR_INVALID_ARG;
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return KSORT_ERR_INVALID_ARG;
+  if (a.type == cudaMemoryTypeDevice && a.device != dev) return KSORT_ERR_INVALID_ARG;
+  return KSORT_OK;
+}
+
+struct DeviceProps {
+  int sms = 0;
+};
+std::map<int, DeviceProps> g_props;
+
+ksort_status_t device_sms(int dev, int *sms) {
+  DeviceProps &p = g_props[dev];
+  if (!p.sms) KS_CUDA(cudaDeviceGetAttribute(&p.sms, cudaDevAttrMultiProcessorCount, dev));
+  *sms = p.sms;
+  return KSORT_OK;
+}
+
+std::map<std::pair<int, int>, int> g_occ;  // (dtype, cutoff) -> CTAs per SM
+
+ksort_status_t full_grid(ksort_dtype_t dt, int dev, const Tuning &tu, int *grid) {
+  int sms = 0;
+  ksort_status_t st = device_sms(dev, &sms);
+  if (st != KSORT_OK) return st;
+  auto key = std::make_pair((int)dt, tu.cutoff);
+  auto it = g_occ.find(key);
+  int occ = 0;
+  if (it == g_occ.end()) {
+    KS_CUDA(ops(dt).max_ctas_per_sm(tu.cutoff, &occ));
+    g_occ[key] = occ;
+  } else {
+    occ = it->second;
+  }
+  if (occ < 1) return KSORT_ERR_INTERNAL;
+  if (tu.ctas_per_sm > 0) occ = std::min(occ, tu.ctas_per_sm);
+  *grid = sms * occ;
+  return KSORT_OK;
+}
+
+SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
+  SortParams p{};
+  p.keys = keys;
+  p.scratch = ws.scratch;
+  p.ctl = ws.ctl;
+  p.items = ws.items;
+  p.ictl = ws.ictl;
+  p.item_cap = ws.item_cap;
+  p.lb = ws.lb;
+  p.lb_cap = ws.lb_cap;
+  p.cutoff = tu.cutoff;
+  p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
+  return p;
+}
+
+ksort_status_t current_device(int *dev) {
+  KS_CUDA(cudaGetDevice(dev));
+  return KSORT_OK;
+}
+
+ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64_t n,
+                              int64_t *key_index, cudaStream_t s, bool in_place) {
+  if (!dtype_ok(dt)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (n < 1 || n > kMaxItemKeys) return KSORT_ERR_INVALID_ARG;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  const size_t kb = key_bytes(dt);
+  if ((st = check_device_ptr(in, kb, dev)) != KSORT_OK) return st;
+  if (!in_place && (st = check_device_ptr(out, kb, dev)) != KSORT_OK) return st;
+  if ((st = check_device_ptr(key_index, 8, dev)) != KSORT_OK) return st;
+  if (!in_place) {
+    const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+    if (a < b + n * kb && b < a + n * kb) return KSORT_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Tuning tu = g_tuning[dt];
+  Workspace *ws = nullptr;
+  Need need = need_for(dt, n, 1);
+  need.item_cap = 64;
+  if (!in_place) need.scratch_bytes = kb;
+  st = get_workspace(dev, s, need, &ws);
+  if (st != KSORT_OK) return st;
+  void *dst = in_place ? ws->scratch : out;
+  if (n == 1) {
+    KS_CUDA(cudaMemsetAsync(key_index, 0, sizeof(int64_t), s));
+    if (!in_place) KS_CUDA(cudaMemcpyAsync(dst, in, kb, cudaMemcpyDeviceToDevice, s));
+    return KSORT_OK;
+  }
+  const long long tiles = ops(dt).tile_count(in, 0, n);
+  if ((unsigned long long)tiles > ws->lb_cap || tiles > 0x7fffffffLL) return KSORT_ERR_INVALID_ARG;
+  KS_CUDA(cudaMemsetAsync(ws->pctl, 0, sizeof(PartCtl) + (size_t)tiles * sizeof(unsigned long long), s));
+  PartParams p{};
+  p.in = in;
+  p.out = dst;
+  p.n = n;
+  p.key_index = reinterpret_cast<long long *>(key_index);
+  p.pctl = ws->pctl;
+  p.lb = ws->lb;
+  p.ctl = ws->ctl;
+  p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
+  KS_CUDA(ops(dt).partition_out(p, (int)tiles, s));
+  if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
+  return KSORT_OK;
+}
+
+ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, int64_t num_arrays,
+                         int64_t total, cudaStream_t s) {
+  if (!dtype_ok(dt)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (total < 0 || num_arrays < 0) return KSORT_ERR_INVALID_ARG;
+  if (!offsets && total > kMaxItemKeys) return KSORT_ERR_INVALID_ARG;
+  if (total <= 1 || num_arrays == 0) return KSORT_OK;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  const size_t kb = key_bytes(dt);
+  if ((st = check_device_ptr(keys, kb, dev)) != KSORT_OK) return st;
+  if (offsets && (st = check_device_ptr(offsets, 8, dev)) != KSORT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Tuning tu = g_tuning[dt];
+  Workspace *ws = nullptr;
+  st = get_workspace(dev, s, need_for(dt, total, num_arrays), &ws);
+  if (st != KSORT_OK) return st;
+  int grid = 0;
+  if ((st = full_grid(dt, dev, tu, &grid)) != KSORT_OK) return st;
+  if (!offsets) {
+    const KernelInfo ki = ops(dt).info();
+    const long long want = std::max<long long>((total + ki.tile_keys - 1) / ki.tile_keys,
+                                               2 * ((total + tu.cutoff - 1) / tu.cutoff));
+    grid = (int)std::max<long long>(1, std::min<long long>(grid, want));
+  }
+  SortParams p = sort_params(*ws, keys, tu);
+  p.offsets = reinterpret_cast<const long long *>(offsets);
+  p.num_roots = offsets ? num_arrays : 1;
+  p.total = total;
+  KS_CUDA(ops(dt).seed(p, s));
+  KS_CUDA(ops(dt).sort(p, grid, s));
+  return KSORT_OK;
+}
+
+// One warp waits for descriptor 0, which stays at generation 0 (never a live epoch).
+__global__ void selftest_wait_kernel(unsigned long long *lb, Control *ctl, unsigned *abort_flag,
+                                     unsigned long long limit_ns) {
+  unsigned long long E = 0, steps = 0;
+  const int st = dev::lookback(lb, 1u, dev::kPartitionEpoch + 1u, limit_ns, abort_flag, &E, &steps);
+  if (threadIdx.x == 0 && st == 1) dev::raise_error(ctl, abort_flag, kDevTimeout, 0x400000000ull);
+}
+
+}  // namespace
+}  // namespace ksort
+
+using namespace ksort;
+
+extern "C" {
+
+ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, int64_t n,
+                               int64_t *key_index_dev, ksort_stream_t stream) {
+  return partition_impl(dtype, keys_dev, nullptr, n, key_index_dev, (cudaStream_t)stream, true);
+}
+
+ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
+                                   int64_t n, int64_t *key_index_dev, ksort_stream_t stream) {
+  return partition_impl(dtype, in_dev, out_dev, n, key_index_dev, (cudaStream_t)stream, false);
+}
+
+ksort_status_t ksort_sort(ksort_dtype_t dtype, void *keys_dev, int64_t n, ksort_stream_t stream) {
+  return sort_impl(dtype, keys_dev, nullptr, 1, n, (cudaStream_t)stream);
+}
+
+ksort_status_t ksort_sort_batched(ksort_dtype_t dtype, void *keys_dev, const int64_t *offsets_dev,
+                                  int64_t num_arrays, int64_t total_keys, ksort_stream_t stream) {
+  if (num_arrays > 0 && !offsets_dev) return KSORT_ERR_INVALID_ARG;
+  return sort_impl(dtype, keys_dev, offsets_dev, num_arrays, total_keys, (cudaStream_t)stream);
+}
+
+ksort_status_t ksort_reserve_workspace(ksort_dtype_t dtype, int64_t max_total_keys,
+                                       int64_t max_arrays, ksort_stream_t stream) {
+  if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (max_total_keys < 0 || max_arrays < 0) return KSORT_ERR_INVALID_ARG;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace *ws = nullptr;
+  st = get_workspace(dev, (cudaStream_t)stream, need_for(dtype, max_total_keys, max_arrays), &ws);
+  if (st != KSORT_OK) return st;
+  int grid = 0;  // also warms the occupancy cache (no queries during graph capture)
+  return full_grid(dtype, dev, g_tuning[dtype], &grid);
+}
+
+ksort_status_t ksort_release_workspace(ksort_stream_t stream) {
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ws.find({dev, (cudaStream_t)stream});
+  if (it == g_ws.end()) return KSORT_OK;
+  KS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (it->second.base) KS_CUDA(cudaFree(it->second.base));
+  g_ws.erase(it);
+  return KSORT_OK;
+}
+
+ksort_status_t ksort_get_device_error(ksort_stream_t stream) {
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  KS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ws.find({dev, (cudaStream_t)stream});
+  if (it == g_ws.end() || !it->second.base) return KSORT_OK;
+  Workspace &ws = it->second;
+  unsigned err = 0;
+  KS_CUDA(cudaMemcpy(&err, &ws.ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err) KS_CUDA(cudaMemset(&ws.ctl->error, 0, sizeof(err)));
+  if (ws.pending_error) {
+    err = ws.pending_error;
+    ws.pending_error = 0;
+  }
+  return (ksort_status_t)err;
+}
+
+ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out) {
+  if (!out) return KSORT_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  KS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_ws.find({dev, (cudaStream_t)stream});
+  if (it == g_ws.end() || !it->second.base) return KSORT_OK;
+  Control c;
+  KS_CUDA(cudaMemcpy(&c, it->second.ctl, sizeof(c), cudaMemcpyDeviceToHost));
+  out->large_items = c.large_items;
+  out->large_keys = c.large_keys;
+  out->tiles = c.tiles;
+  out->small_items = c.small_items;
+  out->small_keys = c.small_keys;
+  out->smem_levels = c.smem_levels;
+  out->lookback_steps = c.lookback_steps;
+  out->items_pushed = c.pushed;
+  return KSORT_OK;
+}
+
+int32_t ksort_max_cutoff(ksort_dtype_t dtype) {
+  if (!dtype_ok(dtype)) return 0;
+  return ops(dtype).info().max_cutoff;
+}
+
+int32_t ksort_tile_keys(ksort_dtype_t dtype) {
+  if (!dtype_ok(dtype)) return 0;
+  return ops(dtype).info().tile_keys;
+}
+
+ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
+  if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (!t) return KSORT_ERR_INVALID_ARG;
+  const int maxc = ops(dtype).info().max_cutoff;
+  if (t->cutoff < 0 || (t->cutoff > 0 && (t->cutoff < 2 || t->cutoff > maxc))) return KSORT_ERR_INVALID_ARG;
+  if (t->ctas_per_sm < 0 || t->spin_limit_ms < 0) return KSORT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Tuning &g = g_tuning[dtype];
+  if (t->cutoff) g.cutoff = t->cutoff;
+  if (t->ctas_per_sm) g.ctas_per_sm = t->ctas_per_sm;
+  if (t->spin_limit_ms) g.spin_limit_ms = t->spin_limit_ms;
+  return KSORT_OK;
+}
+
+ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
+  if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (!out) return KSORT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Tuning &g = g_tuning[dtype];
+  out->cutoff = g.cutoff;
+  out->ctas_per_sm = g.ctas_per_sm;
+  out->spin_limit_ms = g.spin_limit_ms;
+  out->reserved = 0;
+  return KSORT_OK;
+}
+
+ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stream) {
+  if (limit_ms < 1 || limit_ms > 60000) return KSORT_ERR_INVALID_ARG;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace *ws = nullptr;
+  Need need = need_for(KSORT_F32, 1, 1);
+  need.item_cap = 64;
+  need.scratch_bytes = 4;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = get_workspace(dev, s, need, &ws)) != KSORT_OK) return st;
+  KS_CUDA(cudaMemsetAsync(ws->pctl, 0, sizeof(PartCtl) + sizeof(unsigned long long), s));
+  selftest_wait_kernel<<<1, 32, 0, s>>>(ws->lb, ws->ctl, &ws->pctl->abort,
+                                        (unsigned long long)limit_ms * 1000000ull);
+  KS_CUDA(cudaGetLastError());
+  return KSORT_OK;
+}
+
+const char *ksort_status_string(ksort_status_t s) {
+  switch (s) {
+    case KSORT_OK: return "ok";
+    case KSORT_ERR_INVALID_ARG: return "invalid argument";
+    case KSORT_ERR_UNSUPPORTED_DTYPE: return "unsupported dtype";
+    case KSORT_ERR_OUT_OF_MEMORY: return "workspace allocation failed (or needed during graph capture)";
+    case KSORT_ERR_CUDA: return "CUDA runtime error";
+    case KSORT_ERR_TIMEOUT: return "a device-side wait ran past its time limit";
+    case KSORT_ERR_BAD_OFFSETS: return "bad offsets";
+    case KSORT_ERR_WORKSPACE_EXHAUSTED: return "work queue or look-back arena exhausted";
+    case KSORT_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+const char *ksort_last_cuda_error(void) { return g_cuda_error; }
+
+}  // extern "C"

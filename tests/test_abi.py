@@ -1,0 +1,88 @@
+"""The C ABI library loads and exports what include/*.h declares (no GPU needed).
+Also the host-side argument checks that return before any CUDA call."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"KSORT_API\s+[\w\s\*]*?\b(ksort_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1107_3622_gb300 as ks
+    return ks.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("ksort_partition", "ksort_partition_out", "ksort_sort", "ksort_sort_batched",
+                 "ksort_get_device_error", "ksort_reserve_workspace", "ksort_status_string"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_is_in_tree(lib):
+    import paper_1107_3622_gb300 as ks
+    assert os.path.commonpath([ks.library_path(), ROOT]) == ROOT
+
+
+def test_status_strings(lib):
+    import paper_1107_3622_gb300 as ks
+    for code in range(9):
+        assert ks.ksort_status_string(code) and "unknown" not in ks.ksort_status_string(code)
+    assert "unknown" in ks.ksort_status_string(99)
+
+
+def test_host_side_rejections_need_no_gpu(lib):
+    # These return before any CUDA runtime call.
+    assert lib.ksort_sort(0, None, -1, None) == 1          # negative n
+    assert lib.ksort_sort(7, None, 10, None) == 2          # unknown dtype
+    assert lib.ksort_sort(0, None, 1, None) == 0           # n <= 1 is a no-op
+    assert lib.ksort_sort_batched(0, None, None, 3, 10, None) == 1  # offsets missing
+    assert lib.ksort_partition(0, None, 0, None, None) == 1         # n == 0
+    assert lib.ksort_partition(5, None, 4, None, None) == 2
+    assert lib.ksort_selftest_wait_timeout(0, None) == 1
+
+
+def test_tuning_validation(lib):
+    import paper_1107_3622_gb300 as ks
+    for code in (ks.F32, ks.F64, ks.U32):
+        assert ks.ksort_max_cutoff(code) >= 1024
+        assert ks.ksort_tile_keys(code) >= 1024
+        before = ks.ksort_get_tuning(code)
+        with pytest.raises(ks.KSortError):
+            ks.ksort_set_tuning(code, cutoff=ks.ksort_max_cutoff(code) + 1)
+        with pytest.raises(ks.KSortError):
+            ks.ksort_set_tuning(code, cutoff=1)
+        assert ks.ksort_get_tuning(code) == before
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA path are independent: neither includes nor imports the
+    other, and the package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_1107_3622_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h")):
+            text = open(path).read()
+            assert "oracle" not in re.findall(r"^\s*(?:import|from)\s+(\w+)", text, re.M), path
+            assert "ksort_ref" not in text, path
+    for path in glob.glob(os.path.join(ROOT, "oracle", "*")):
+        if os.path.isfile(path) and path.endswith((".py", ".c", ".h")):
+            text = open(path).read()
+            assert "paper_1107_3622_gb300" not in text and "ksort.h" not in text, path
