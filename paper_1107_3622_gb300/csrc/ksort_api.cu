@@ -135,7 +135,7 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   const size_t o_ctl = off;
   off = align_up(off + sizeof(Control), 256);
   const size_t o_pctl = off;
-  off += sizeof(PartCtl);  // look-back follows directly: one memset clears both
+  off = align_up(off + sizeof(PartCtl), 256);
   const size_t o_lb = off;
   off = align_up(off + lb_cap * sizeof(unsigned long long), 256);
   const size_t o_items = off;
@@ -271,7 +271,6 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   }
   const long long tiles = ops(dt).tile_count(in, 0, n);
   if ((unsigned long long)tiles > ws->lb_cap || tiles > 0x7fffffffLL) return KSORT_ERR_INVALID_ARG;
-  KS_CUDA(cudaMemsetAsync(ws->pctl, 0, sizeof(PartCtl) + (size_t)tiles * sizeof(unsigned long long), s));
   PartParams p{};
   p.in = in;
   p.out = dst;
@@ -324,7 +323,7 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
 __global__ void selftest_wait_kernel(unsigned long long *lb, Control *ctl, unsigned *abort_flag,
                                      unsigned long long limit_ns) {
   unsigned long long E = 0, steps = 0;
-  const int st = dev::lookback(lb, 1u, dev::kPartitionEpoch + 1u, limit_ns, abort_flag, &E, &steps);
+  const int st = dev::lookback(lb, 1u, 0xffffffffu, limit_ns, abort_flag, &E, &steps);
   if (threadIdx.x == 0 && st == 1) dev::raise_error(ctl, abort_flag, kDevTimeout, 0x400000000ull);
 }
 
@@ -473,8 +472,9 @@ ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stre
   need.scratch_bytes = 4;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = get_workspace(dev, s, need, &ws)) != KSORT_OK) return st;
-  KS_CUDA(cudaMemsetAsync(ws->pctl, 0, sizeof(PartCtl) + sizeof(unsigned long long), s));
-  selftest_wait_kernel<<<1, 32, 0, s>>>(ws->lb, ws->ctl, &ws->pctl->abort,
+  KS_CUDA(cudaMemsetAsync(ws->lb, 0, sizeof(unsigned long long), s));
+  KS_CUDA(cudaMemsetAsync(&ws->ctl->abort, 0, sizeof(unsigned), s));
+  selftest_wait_kernel<<<1, 32, 0, s>>>(ws->lb, ws->ctl, &ws->ctl->abort,
                                         (unsigned long long)limit_ms * 1000000ull);
   KS_CUDA(cudaGetLastError());
   return KSORT_OK;

@@ -103,10 +103,13 @@ __host__ __device__ __forceinline__ unsigned tile_count(const K *buf, long long 
 }
 
 // Look-back descriptor: [63:32] epoch, [31] inclusive-prefix flag, [30:0] value.
-// Sorts number their generations 1 .. kPartitionEpoch - 1; a standalone partition
-// clears its descriptors first and always uses kPartitionEpoch, so descriptors left by
-// one kind of call never look valid to the other.
-constexpr unsigned kPartitionEpoch = 0xfffffff0u;
+// Sorts number their generations 1 .. 2^31 - 1 and standalone partitions
+// 2^31 .. 2^32 - 1, so descriptors left by one kind of call never look valid to the
+// other; zeroed memory (epoch 0) is never valid.
+constexpr unsigned kPartitionEpoch = 0x80000000u;
+__host__ __device__ __forceinline__ unsigned partition_epoch(unsigned gen) {
+  return kPartitionEpoch | (gen & 0x7fffffffu);
+}
 __device__ __forceinline__ unsigned long long lb_pack(unsigned epoch, bool inclusive,
                                                        unsigned v) {
   return ((unsigned long long)epoch << 32) | ((unsigned long long)inclusive << 31) |
@@ -734,37 +737,56 @@ __global__ void seed_kernel(SortParams p) {
 }
 
 // Standalone out-of-place partition (ksort_partition_out): one CTA per tile, tiles
-// claimed in launch order through a ticket so that look-back only waits on running CTAs.
+// claimed in launch order through a ticket so that look-back only waits on CTAs that
+// are already running. Every CTA counts itself done, even after an abort, so the last
+// one can hand a clean state to the next call.
 template <typename K, int BLOCK, int IPT>
 __global__ void __launch_bounds__(BLOCK) partition_kernel(PartParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ TileShared<BLOCK> sh;
-  __shared__ unsigned t_sh;
+  __shared__ unsigned t_sh, gen_sh;
+  __shared__ unsigned long long base_sh;
   const K *in = static_cast<const K *>(p.in);
   K *out = static_cast<K *>(p.out);
-  if (threadIdx.x == 0) t_sh = atomicAdd(&p.pctl->ticket, 1u);
+  PartCtl *pc = p.pctl;
+  if (threadIdx.x == 0) {
+    const unsigned long long base = ld_relaxed(&pc->base);
+    gen_sh = ld_relaxed(&pc->gen);
+    base_sh = base;
+    t_sh = (unsigned)(atomicAdd(&pc->ticket, 1ull) - base);
+  }
   __syncthreads();
   const unsigned t = t_sh;
+  const unsigned long long base = base_sh;
   const unsigned ntiles = gridDim.x;
   unsigned long long less = 0, steps = 0;
-  const bool ok = partition_tile<K, BLOCK, IPT>(in, out, 0, p.n, t, p.lb, kPartitionEpoch,
-                                                p.spin_limit_ns,
-                                                p.ctl, &p.pctl->abort, reinterpret_cast<K *>(smem),
-                                                sh, &less, &steps);
-  if (!ok) return;
+  bool ok = false;
+  if (t < ntiles) {
+    ok = partition_tile<K, BLOCK, IPT>(in, out, 0, p.n, t, p.lb, partition_epoch(gen_sh),
+                                       p.spin_limit_ns, p.ctl, &pc->abort,
+                                       reinterpret_cast<K *>(smem), sh, &less, &steps);
+  } else if (threadIdx.x == 0) {
+    raise_error(p.ctl, &pc->abort, kDevInternal, 0x800000000ull | t);
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (t == ntiles - 1) {
-      atomicExch(&p.pctl->less, less);
+    if (ok && t == ntiles - 1) {
+      atomicExch(&pc->less, less);
       __threadfence();
     }
-    const unsigned old = atomicAdd(&p.pctl->done, 1u);
+    const unsigned long long old = atomicAdd(&pc->done, 1ull) - base;
     if (old == ntiles - 1) {
       __threadfence();
-      const unsigned long long c = ld_acquire(&p.pctl->less);
-      out[c] = __ldcg(in);  // Step 4
-      *p.key_index = (long long)c;
+      if (ld_relaxed(&pc->abort) == 0u) {
+        const unsigned long long c = ld_acquire(&pc->less);
+        out[c] = __ldcg(in);  // Step 4
+        *p.key_index = (long long)c;
+      }
+      // Every CTA of this call has read base and gen and finished: start the next call.
+      atomicExch(&pc->base, base + ntiles);
+      atomicExch(&pc->gen, gen_sh + 1u);
+      atomicExch(&pc->abort, 0u);
     }
   }
 }

@@ -62,13 +62,18 @@ struct alignas(16) ItemCtl {
   unsigned long long less;  // #{x < key} of the item, written by its last tile
 };
 
-// Control of one standalone partition call.
+// State of the standalone partition, carried from call to call on one stream: tickets
+// and completions count up forever; `base` is their value when the current call
+// started and `gen` numbers the call (its look-back descriptors carry the generation).
+// The last CTA of a call advances `base` and `gen` and clears `abort`, so no memset is
+// needed between calls.
 struct alignas(64) PartCtl {
-  unsigned ticket;
-  unsigned done;
-  unsigned abort;
-  unsigned pad;
+  unsigned long long ticket;
+  unsigned long long done;
+  unsigned long long base;
   unsigned long long less;
+  unsigned gen;
+  unsigned abort;
 };
 
 struct SortParams {
