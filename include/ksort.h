@@ -111,6 +111,10 @@ typedef struct {
     uint64_t smem_levels;   /* partition levels run inside shared memory (all items)   */
     uint64_t lookback_steps;/* 32-wide look-back windows examined                      */
     uint64_t items_pushed;  /* work-queue entries used                                 */
+    uint64_t cycles_fetch;  /* SM cycles of the sort kernel's CTAs (summed) spent       */
+    uint64_t cycles_small;  /*   waiting for / claiming work, finishing small items,    */
+    uint64_t cycles_tiles;  /*   running tile passes, and placing keys / queueing the   */
+    uint64_t cycles_finish; /*   two sides (Step 4 and Steps 5-6)                       */
 } ksort_stats_t;
 KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out);
 

@@ -65,7 +65,7 @@ struct Tuning {
 };
 
 std::mutex g_mu;
-Tuning g_tuning[3] = {{4096, 0, 2000}, {4096, 0, 2000}, {4096, 0, 2000}};
+Tuning g_tuning[3] = {{8192, 0, 2000}, {4096, 0, 2000}, {8192, 0, 2000}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -77,6 +77,7 @@ struct Workspace {
   unsigned long long lb_cap = 0;
   Item *items = nullptr;
   ItemCtl *ictl = nullptr;
+  unsigned long long *tmap = nullptr, *small_q = nullptr;
   unsigned long long item_cap = 0;
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -142,6 +143,10 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   off = align_up(off + item_cap * sizeof(Item), 256);
   const size_t o_ictl = off;
   off = align_up(off + item_cap * sizeof(ItemCtl), 256);
+  const size_t o_tmap = off;
+  off = align_up(off + lb_cap * sizeof(unsigned long long), 256);
+  const size_t o_sq = off;
+  off = align_up(off + item_cap * sizeof(unsigned long long), 256);
   const size_t meta = off;
   const size_t o_scr = off;
   off = align_up(off + scratch_bytes, 256);
@@ -165,6 +170,8 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   ws.lb_cap = lb_cap;
   ws.items = reinterpret_cast<Item *>(b + o_items);
   ws.ictl = reinterpret_cast<ItemCtl *>(b + o_ictl);
+  ws.tmap = reinterpret_cast<unsigned long long *>(b + o_tmap);
+  ws.small_q = reinterpret_cast<unsigned long long *>(b + o_sq);
   ws.item_cap = item_cap;
   ws.scratch = b + o_scr;
   ws.scratch_bytes = scratch_bytes;
@@ -227,6 +234,8 @@ SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
   p.ctl = ws.ctl;
   p.items = ws.items;
   p.ictl = ws.ictl;
+  p.tmap = ws.tmap;
+  p.small_q = ws.small_q;
   p.item_cap = ws.item_cap;
   p.lb = ws.lb;
   p.lb_cap = ws.lb_cap;
@@ -420,7 +429,11 @@ ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out) {
   out->small_keys = c.small_keys;
   out->smem_levels = c.smem_levels;
   out->lookback_steps = c.lookback_steps;
-  out->items_pushed = c.pushed;
+  out->items_pushed = c.pushed;  // pool slots: large and small items
+  out->cycles_fetch = c.cyc_fetch;
+  out->cycles_small = c.cyc_small;
+  out->cycles_tiles = c.cyc_tile;
+  out->cycles_finish = c.cyc_finish;
   return KSORT_OK;
 }
 

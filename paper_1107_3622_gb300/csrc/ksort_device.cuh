@@ -52,6 +52,9 @@ __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
 __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -175,68 +178,87 @@ __device__ __forceinline__ int lookback(const unsigned long long *lb, unsigned t
   }
 }
 
-// One tile pass of the partition of [begin, end) from `src` to `dst`.
-// Less keys of tile t land at dst[begin + E_t ...], >= keys at the right end,
-// dst[end - PG_t - G_t ...] with PG_t the >= keys of earlier tiles; so the key's index
-// begin + #{x < key} is left free. Returns false if the call was aborted or timed out.
-// Requires a __syncthreads() between consecutive calls (shared staging reuse).
+// Writes count keys from shared memory (sm[0..count)) to global g[0..count): scalar
+// stores up to the first 16-byte boundary of g, then one 128-bit store per VEC keys.
+template <typename K, int BLOCK>
+__device__ __forceinline__ void copy_out(const K *sm, K *g, unsigned count) {
+  constexpr int VEC = Vec<K>::N;
+  using V = typename Vec<K>::T;
+  const int tid = threadIdx.x;
+  unsigned head = (unsigned)(((16u - (reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) / sizeof(K));
+  if (head > count) head = count;
+  if (tid < (int)head) g[tid] = sm[tid];
+  const unsigned nvec = (count - head) / VEC;
+  V *gv = reinterpret_cast<V *>(g + head);
+  for (unsigned v = tid; v < nvec; v += BLOCK) {
+    K x[VEC];
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) x[l] = sm[head + v * VEC + l];
+    V q;
+    if constexpr (VEC == 4) {
+      q.x = x[0]; q.y = x[1]; q.z = x[2]; q.w = x[3];
+    } else {
+      q.x = x[0]; q.y = x[1];
+    }
+    gv[v] = q;
+  }
+  for (unsigned k = head + nvec * VEC + tid; k < count; k += BLOCK) g[k] = sm[k];
+}
+
+// One tile pass of the partition of [begin, end) from `src` to `dst` (Steps 1-4 for
+// the keys of one tile). The tile is staged in shared memory (`sin`, TILE keys); each
+// warp classifies a contiguous TILE/NW slice with ballots, twice: once to count, and,
+// after the look-back has given the keys of earlier tiles, again to scatter into
+// `sout` in partitioned order. Less keys of tile t land at dst[begin + E_t ...], the
+// others at the right end, dst[end - PG_t - G_t ...] with PG_t the >= keys of earlier
+// tiles, so the key's index begin + #{x < key} stays free. Returns false if the call
+// was aborted or timed out. Needs a __syncthreads() between consecutive calls.
 template <typename K, int BLOCK, int IPT>
 __device__ __forceinline__ bool partition_tile(
     const K *__restrict__ src, K *__restrict__ dst, long long begin, long long end, unsigned t,
     unsigned long long *__restrict__ lb, unsigned epoch, unsigned long long limit_ns,
-    Control *ctl, unsigned *abort_flag, K *stage, TileShared<BLOCK> &sh,
+    Control *ctl, unsigned *abort_flag, K *sin, TileShared<BLOCK> &sh,
     unsigned long long *less_through_tile, unsigned long long *lb_steps) {
   constexpr int VEC = Vec<K>::N;
-  constexpr int VPT = IPT / VEC;
   constexpr int TILE = BLOCK * IPT;
   constexpr int NW = BLOCK / 32;
-  static_assert(IPT % VEC == 0 && IPT <= 32, "bad IPT");
+  constexpr int SLICE = TILE / NW;  // keys per warp
+  static_assert(IPT % VEC == 0 && SLICE % 32 == 0, "bad tile shape");
   using V = typename Vec<K>::T;
+  K *sout = sin + TILE;
 
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const K key = __ldcg(src + begin);  // Step 1: the first element is the key
   const long long first = begin + 1;
   const long long base = tile_base(src, begin);
   const long long lo = base + (long long)t * TILE;
+  // valid positions of this tile: [vlo, vhi) relative to lo
+  const int vlo = (int)(first > lo ? first - lo : 0);
+  const int vhi = (int)(end - lo < TILE ? end - lo : TILE);
 
-  K x[IPT];
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    const long long e0 = lo + ((long long)v * BLOCK + tid) * VEC;
-    if (e0 >= first && e0 + VEC <= end) {
-      const V q = __ldcg(reinterpret_cast<const V *>(src + e0));
-      unpack<K>(q, &x[v * VEC]);
+  // stage the tile: 128-bit loads for whole vectors, single loads at the two edges
+  for (int v = tid; v < TILE / VEC; v += BLOCK) {
+    const int k0 = v * VEC;
+    if (k0 >= vlo && k0 + VEC <= vhi) {
+      *reinterpret_cast<V *>(sin + k0) = __ldcg(reinterpret_cast<const V *>(src + lo + k0));
     } else {
 #pragma unroll
-      for (int l = 0; l < VEC; ++l) {
-        const long long e = e0 + l;
-        x[v * VEC + l] = (e >= first && e < end) ? __ldcg(src + e) : K(0);
-      }
+      for (int l = 0; l < VEC; ++l)
+        if (k0 + l >= vlo && k0 + l < vhi) sin[k0 + l] = __ldcg(src + lo + k0 + l);
     }
   }
+  __syncthreads();
 
-  // Step 3 for every element; ranks within the warp from ballots.
+  // pass 1: Step 3 counts per warp
   const unsigned lt = lanemask_lt();
-  unsigned rank[IPT];
-  unsigned lessbits = 0, validbits = 0;
   unsigned wl = 0, wg = 0;
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-#pragma unroll
-    for (int l = 0; l < VEC; ++l) {
-      const int i = v * VEC + l;
-      const long long e = lo + ((long long)v * BLOCK + tid) * VEC + l;
-      const bool valid = e >= first && e < end;
-      const bool le = valid && goes_left(key, x[i]);
-      const bool ge = valid && !le;
-      const unsigned ml = __ballot_sync(kFull, le);
-      const unsigned mg = __ballot_sync(kFull, ge);
-      rank[i] = le ? wl + __popc(ml & lt) : wg + __popc(mg & lt);
-      wl += __popc(ml);
-      wg += __popc(mg);
-      lessbits |= (unsigned)le << i;
-      validbits |= (unsigned)valid << i;
-    }
+#pragma unroll 4
+  for (int c = 0; c < SLICE; c += 32) {
+    const int k = w * SLICE + c + lane;
+    const bool valid = k >= vlo && k < vhi;
+    const bool le = valid && goes_left(key, sin[k]);
+    wl += __popc(__ballot_sync(kFull, le));
+    wg += __popc(__ballot_sync(kFull, valid && !le));
   }
   if (lane == 0) {
     sh.wl[w] = wl;
@@ -273,228 +295,377 @@ __device__ __forceinline__ bool partition_tile(
         *lb_steps += steps;
       }
     }
-    const bool ok = status == 0;
     if (lane == 0) {
       if (status == 1) raise_error(ctl, abort_flag, kDevTimeout, 0x100000000ull | t);
       sh.L = L;
       sh.G = G;
       sh.E = E;
-      sh.abort = ok ? 0 : 1;
+      sh.abort = status == 0 ? 0 : 1;
     }
   }
   __syncthreads();
   if (sh.abort) return false;
 
+  // pass 2: the same classification, scattered into sout in partitioned order
   const unsigned L = sh.L, G = sh.G;
   const unsigned long long E = sh.E;
-  const unsigned wlx = sh.wl[w], wgx = sh.wg[w];
-#pragma unroll
-  for (int i = 0; i < IPT; ++i) {
-    if ((validbits >> i) & 1u) {
-      const unsigned slot = ((lessbits >> i) & 1u) ? wlx + rank[i] : L + wgx + rank[i];
-      stage[slot] = x[i];
-    }
+  unsigned rl = sh.wl[w], rg = L + sh.wg[w];
+#pragma unroll 4
+  for (int c = 0; c < SLICE; c += 32) {
+    const int k = w * SLICE + c + lane;
+    const bool valid = k >= vlo && k < vhi;
+    const K x = valid ? sin[k] : K(0);
+    const bool le = valid && goes_left(key, x);
+    const unsigned ml = __ballot_sync(kFull, le), mg = __ballot_sync(kFull, valid && !le);
+    if (valid) sout[le ? rl + __popc(ml & lt) : rg + __popc(mg & lt)] = x;
+    rl += __popc(ml);
+    rg += __popc(mg);
   }
   __syncthreads();
 
-  const long long PV = t == 0 ? 0 : lo - first;  // classified elements in earlier tiles
+  const long long PV = t == 0 ? 0 : lo - first;  // classified keys in earlier tiles
   const long long PG = PV - (long long)E;        // of which >= key
   const long long lbase = begin + (long long)E;
   const long long gbase = end - PG - (long long)G;
-  const unsigned total = L + G;
-  bool bad = false;
-  for (unsigned k = tid; k < total; k += BLOCK) {
-    const long long d = k < L ? lbase + k : gbase + (k - L);
-    if (d >= begin && d < end) {
-      dst[d] = stage[k];
-    } else {
-      bad = true;  // only with inconsistent prefixes; never write outside the item
-    }
+  if (lbase < begin || lbase + L > end || gbase < begin || gbase + G > end) {
+    // only with inconsistent prefixes; never write outside the item
+    if (tid == 0) raise_error(ctl, abort_flag, kDevInternal, 0x500000000ull | t);
+    return false;
   }
-  if (bad) raise_error(ctl, abort_flag, kDevInternal, 0x500000000ull | t);
+  copy_out<K, BLOCK>(sout, dst + lbase, L);
+  copy_out<K, BLOCK>(sout + L, dst + gbase, G);
   *less_through_tile = E + L;
   return true;
 }
 
 // ----------------------------------------------------------------------------- smem
-// Shared-memory finisher: sorts m <= cap keys with the K-sort key rule, all segments of
-// one recursion level at a time. Each segment [s, s_end) uses its first element as the
-// key; its less keys keep their order at s.., the key lands at s + L, the >= keys keep
-// their order after it. Segments of one key are final. The whole level is one
-// block-wide pass: ballot counts, one scan, then a scatter into the other buffer.
-template <int BLOCK, int JMAX>
-struct SmemShared {
-  unsigned cnt[JMAX * (BLOCK / 32)];
-  int active;
-  int next_active;
-  int bad;
+// Shared-memory finisher for one small sub-array (m <= cutoff keys), run by one CTA.
+// The keys are loaded into buffer A; every recursion level then runs on WARPS, with no
+// CTA barrier: a warp takes a segment [s, s + n) from a CTA-local queue and applies
+// Steps 1-4 to it (key = its first element; x goes right when key <= x) from one
+// shared buffer into the other, then Steps 5-6 depth first: it keeps one side, queues
+// the other, and finishes sides of at most 32 keys in registers by the same rule.
+// Every key that reaches its final index is written there in buffer A, which is
+// copied out once all warps are done.
+// Queued segments hold more than 32 keys and are disjoint, so at most cutoff / 33 are
+// live at once: 512 slots cover cutoffs up to 16896 keys.
+constexpr int kSmallQueue = 512;
+constexpr int kMaxSmallCutoff = 16384;
+// Segments above this size are partitioned by the whole CTA, smaller ones by one warp.
+constexpr int kBlockSegment = 1024;
+constexpr int kBigStack = kMaxSmallCutoff / kBlockSegment + 2;
+
+struct SmallShared {
+  unsigned long long ring[kSmallQueue];
+  unsigned long long big[kBigStack];  // segments for CTA-wide partitions
+  unsigned wl[32], wg[32];            // per-warp counts of a CTA-wide partition
+  int head, tail, pending, bad, nbig, L;
 };
 
 template <typename K>
-__host__ __device__ constexpr size_t smem_finisher_bytes(int cap) {
-  // two key buffers, two u16 segment-start buffers, one u16 per-segment slot array
-  return (size_t)cap * (2 * sizeof(K) + 3 * sizeof(unsigned short)) + 64;
+__host__ __device__ constexpr size_t smem_finisher_bytes(int cap, int warps) {
+  // buffers A and B, then per-warp scratch for the 32-key register sorts
+  return (size_t)2 * cap * sizeof(K) + (size_t)warps * 32 * (sizeof(K) + sizeof(unsigned)) + 64;
 }
 
-// Returns false if a consistency check failed (the output is then not sorted).
-template <typename K, int BLOCK, int JMAX>
-__device__ bool smem_ksort(const K *__restrict__ src, K *__restrict__ out, int m, int cap,
-                           unsigned char *smem, SmemShared<BLOCK, JMAX> &sh,
-                           unsigned long long *levels) {
-  constexpr int NW = BLOCK / 32;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  K *k0 = reinterpret_cast<K *>(smem);
-  K *k1 = k0 + cap;
-  unsigned short *s0 = reinterpret_cast<unsigned short *>(k1 + cap);
-  unsigned short *s1 = s0 + cap;
-  unsigned short *slot = s1 + cap;
+// Steps 1-4 by one warp on X[s .. s+n): less keys to Y[s ..] upward, the others to
+// Y[s+n-1 ..] downward; returns the number of less keys L (the key's offset).
+template <typename K>
+__device__ __forceinline__ int warp_partition(const K *X, K *Y, int s, int n, K key) {
+  const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-
-  for (int e = tid; e < m; e += BLOCK) {
-    k0[e] = __ldcg(src + e);
-    s0[e] = 0;
+  const int e = s + n;
+  int L = 0, G = 0;
+  for (int i0 = s + 1; i0 < e; i0 += 64) {
+    const int ia = i0 + lane, ib = ia + 32;
+    const bool va = ia < e, vb = ib < e;
+    const K xa = va ? X[ia] : K(0);
+    const K xb = vb ? X[ib] : K(0);
+    const bool la = va && goes_left(key, xa);
+    const bool lb = vb && goes_left(key, xb);
+    const unsigned mla = __ballot_sync(kFull, la), mga = __ballot_sync(kFull, va && !la);
+    const unsigned mlb = __ballot_sync(kFull, lb), mgb = __ballot_sync(kFull, vb && !lb);
+    if (va) Y[la ? s + L + __popc(mla & lt) : e - 1 - G - __popc(mga & lt)] = xa;
+    L += __popc(mla);
+    G += __popc(mga);
+    if (vb) Y[lb ? s + L + __popc(mlb & lt) : e - 1 - G - __popc(mgb & lt)] = xb;
+    L += __popc(mlb);
+    G += __popc(mgb);
   }
+  __syncwarp();
+  return L;
+}
+
+// Steps 1-6 for n <= 32 keys held one per lane: every segment of the warp is
+// partitioned around its first element in the same step, until all segments hold one
+// key. X[s..s+n) in, A[s..s+n) out (X may equal A).
+template <typename K>
+__device__ __forceinline__ void warp_tiny_ksort(const K *X, K *A, int s, int n, K *wk,
+                                                unsigned *wseg) {
+  const int lane = threadIdx.x & 31;
+  const bool act = lane < n;
+  const unsigned lt = lanemask_lt();
+  K x = act ? X[s + lane] : K(0);
+  int lo = 0, hi = n;
+  for (int level = 0; level < 32; ++level) {
+    if (!__any_sync(kFull, act && lane == lo && hi - lo >= 2)) break;
+    const K key = __shfl_sync(kFull, x, lo);
+    const bool in_big = act && hi - lo >= 2;
+    const bool is_key = lane == lo;
+    const bool lf = in_big && !is_key && goes_left(key, x);
+    const unsigned ml = __ballot_sync(kFull, lf);
+    const unsigned segmask = (hi >= 32 ? kFull : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+    const int Lc = __popc(ml & segmask);
+    const int rl = __popc(ml & segmask & lt);
+    int dest = lane, nlo = lo, nhi = hi;
+    if (in_big) {
+      if (is_key) {
+        dest = lo + Lc;
+        nlo = dest;
+        nhi = dest + 1;
+      } else if (lf) {
+        dest = lo + rl;
+        nhi = lo + Lc;
+      } else {
+        dest = lo + Lc + 1 + (lane - lo - 1 - rl);
+        nlo = lo + Lc + 1;
+      }
+    }
+    if (act) {
+      wk[dest] = x;
+      wseg[dest] = (unsigned)nlo | ((unsigned)nhi << 8);
+    }
+    __syncwarp();
+    if (act) {
+      x = wk[lane];
+      const unsigned q = wseg[lane];
+      lo = (int)(q & 0xffu);
+      hi = (int)(q >> 8);
+    }
+    __syncwarp();
+  }
+  if (act) A[s + lane] = x;
+  __syncwarp();
+}
+
+__device__ __forceinline__ unsigned long long seg_pack(int s, int n, int par) {
+  return ((unsigned long long)(unsigned)s << 32) | ((unsigned long long)(unsigned)n << 1) |
+         (unsigned long long)par;
+}
+
+// Lane 0 queues a segment of more than 32 keys.
+__device__ __forceinline__ void small_push(SmallShared &q, int s, int n, int par) {
+  atomicAdd(&q.pending, 1);
+  const int slot = atomicAdd(&q.tail, 1);
+  __threadfence_block();
+  atomicExch(&q.ring[slot % kSmallQueue], seg_pack(s, n, par));
+}
+
+// Lane 0 claims the next queued segment; returns 0 once the CTA's work is done.
+__device__ __forceinline__ unsigned long long small_pop(SmallShared &q) {
+  volatile SmallShared &v = q;
+  for (unsigned spins = 0;; ++spins) {
+    const int h = v.head;
+    if (h < v.tail) {
+      if (atomicCAS(&q.head, h, h + 1) == h) {
+        unsigned long long e = 0;
+        for (unsigned w = 0; (e = atomicExch(&q.ring[h % kSmallQueue], 0ull)) == 0ull; ++w) {
+          if (w > (1u << 24)) {  // the pusher reserved the slot: it cannot stay empty
+            q.bad = 1;
+            return 0;
+          }
+        }
+        __threadfence_block();
+        return e;
+      }
+    } else if (v.pending == 0 || v.bad) {
+      return 0;
+    }
+    if (spins > (1u << 26)) {
+      q.bad = 1;
+      return 0;
+    }
+    __nanosleep(16);
+  }
+}
+
+// Steps 1-4 by the whole CTA on X[s .. s+n): each warp classifies a contiguous run of
+// 32-key chunks twice (count, then scatter after a scan of the warp counts). Same
+// output layout as warp_partition. Returns L; contains three CTA barriers.
+template <typename K, int BLOCK>
+__device__ __forceinline__ int block_partition(const K *X, K *Y, int s, int n, K key,
+                                               SmallShared &q) {
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  const int e = s + n;
+  const int nch = (n - 1 + 31) / 32;
+  const int per = (nch + NW - 1) / NW;
+  const int c0 = w * per, c1 = min(nch, c0 + per);
+  unsigned wl = 0, wg = 0;
+  for (int c = c0; c < c1; ++c) {
+    const int i = s + 1 + c * 32 + lane;
+    const bool v = i < e;
+    const bool le = v && goes_left(key, X[i]);
+    wl += __popc(__ballot_sync(kFull, le));
+    wg += __popc(__ballot_sync(kFull, v && !le));
+  }
+  if (lane == 0) {
+    q.wl[w] = wl;
+    q.wg[w] = wg;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const unsigned a0 = lane < NW ? q.wl[lane] : 0u, b0 = lane < NW ? q.wg[lane] : 0u;
+    unsigned a = a0, b = b0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned ua = __shfl_up_sync(kFull, a, o), ub = __shfl_up_sync(kFull, b, o);
+      if (lane >= o) { a += ua; b += ub; }
+    }
+    if (lane < NW) {
+      q.wl[lane] = a - a0;
+      q.wg[lane] = b - b0;
+    }
+    if (lane == 31) q.L = (int)a;
+  }
+  __syncthreads();
+  unsigned rl = q.wl[w], rg = q.wg[w];
+  for (int c = c0; c < c1; ++c) {
+    const int i = s + 1 + c * 32 + lane;
+    const bool v = i < e;
+    const K x = v ? X[i] : K(0);
+    const bool le = v && goes_left(key, x);
+    const unsigned ml = __ballot_sync(kFull, le), mg = __ballot_sync(kFull, v && !le);
+    if (v) Y[le ? s + rl + __popc(ml & lt) : e - 1 - rg - __popc(mg & lt)] = x;
+    rl += __popc(ml);
+    rg += __popc(mg);
+  }
+  const int L = q.L;
+  __syncthreads();
+  return L;
+}
+
+// Sorts src[0..m) into out[0..m) (they may alias) with the K-sort rule.
+template <typename K, int BLOCK>
+__device__ bool smem_ksort(const K *__restrict__ src, K *__restrict__ out, int m, int cap,
+                           unsigned char *smem, SmallShared &q, unsigned long long *segments) {
+  constexpr int NW = BLOCK / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  K *A = reinterpret_cast<K *>(smem);
+  K *B = A + cap;
+  K *wk = B + cap + warp * 32;
+  unsigned *wseg = reinterpret_cast<unsigned *>(B + cap + NW * 32) + warp * 32;
+
+  for (int e = tid; e < m; e += BLOCK) A[e] = __ldcg(src + e);
+  for (int i = tid; i < kSmallQueue; i += BLOCK) q.ring[i] = 0ull;
   if (tid == 0) {
-    sh.active = m >= 2;
-    sh.bad = 0;
+    q.head = 0;
+    q.tail = 0;
+    q.pending = 0;
+    q.bad = 0;
   }
   __syncthreads();
-
-  const int J = (m + BLOCK - 1) / BLOCK;
-  unsigned long long nlev = 0;
-  while (sh.active) {
-    // Every level shrinks each unfinished segment by at least its key, so m levels
-    // always suffice; more means corrupted state: stop rather than loop.
-    if (++nlev > (unsigned long long)m) {
-      if (tid == 0) sh.bad = 1;
-      break;
-    }
-    // A: classify against the segment's first element; ballot counts per (chunk, warp).
-    unsigned bal[JMAX];
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-      bal[j] = 0;
-      if (j < J) {
-        const int e = j * BLOCK + tid;
-        bool lf = false;
-        if (e < m) {
-          const int s = s0[e];
-          lf = e != s && goes_left(k0[s], k0[e]);
-        }
-        bal[j] = __ballot_sync(kFull, lf);
-        if (lane == 0) sh.cnt[j * NW + w] = __popc(bal[j]);
-      }
-    }
-    if (tid == 0) sh.next_active = 0;
-    __syncthreads();
-    // B: exclusive scan of the counts in element order (one warp).
-    if (w == 0) {
-      const int n = J * NW;
-      constexpr int PER = (JMAX * NW + 31) / 32;
-      unsigned loc[PER];
-      unsigned sum = 0;
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int i = lane * PER + q;
-        loc[q] = i < n ? sh.cnt[i] : 0u;
-        sum += loc[q];
-      }
-      unsigned inc = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned u = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += u;
-      }
-      unsigned run = inc - sum;
-#pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int i = lane * PER + q;
-        if (i < n) sh.cnt[i] = run;
-        run += loc[q];
-      }
+  unsigned long long nseg = 0;
+  if (m <= 32) {
+    if (warp == 0) warp_tiny_ksort(A, A, 0, m, wk, wseg);
+    nseg = 1;
+  } else {
+    // CTA-wide partitions while segments are large (the top levels of the item)
+    if (tid == 0) {
+      q.nbig = 0;
+      if (m > kBlockSegment) q.big[q.nbig++] = seg_pack(0, m, 0);
+      else small_push(q, 0, m, 0);
     }
     __syncthreads();
-    // C: segment heads record the prefix at their start.
+    while (q.nbig > 0) {
+      const unsigned long long e = q.big[q.nbig - 1];
+      const int s = (int)(e >> 32), n = (int)((e >> 1) & 0x7fffffffu), par = (int)(e & 1ull);
+      __syncthreads();
+      const K *X = par ? B : A;
+      K *Y = par ? A : B;
+      const K key = X[s];
+      const int L = block_partition<K, BLOCK>(X, Y, s, n, key, q);
+      ++nseg;
+      const int cp = par ^ 1;
+      if (tid == 0) {
+        A[s + L] = key;
+        --q.nbig;
 #pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-      if (j < J) {
-        const int e = j * BLOCK + tid;
-        if (e < m && s0[e] == e) slot[e] = (unsigned short)(sh.cnt[j * NW + w] + __popc(bal[j] & lt));
-      }
-    }
-    __syncthreads();
-    unsigned ps[JMAX];
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-      ps[j] = 0;
-      if (j < J) {
-        const int e = j * BLOCK + tid;
-        if (e < m) ps[j] = slot[s0[e]];
-      }
-    }
-    __syncthreads();
-    // D: the last element of each segment stores the segment's less count L.
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-      if (j < J) {
-        const int e = j * BLOCK + tid;
-        if (e < m) {
-          const int s = s0[e];
-          if (e == m - 1 || s0[e + 1] != s) {
-            const unsigned pre = sh.cnt[j * NW + w] + __popc(bal[j] & lt);
-            slot[s] = (unsigned short)(pre + ((bal[j] >> lane) & 1u) - ps[j]);
-          }
+        for (int c = 0; c < 2; ++c) {
+          const int cs = c ? s + L + 1 : s, cn = c ? n - L - 1 : L;
+          if (cn > kBlockSegment) q.big[q.nbig++] = seg_pack(cs, cn, cp);
+          else if (cn > 32) small_push(q, cs, cn, cp);
+          else if (cn == 1 && cp) A[cs] = Y[cs];
         }
       }
+      if (warp < 2) {  // warps 0 and 1 finish a side of at most 32 keys at once
+        const int cs = warp ? s + L + 1 : s, cn = warp ? n - L - 1 : L;
+        if (cn >= 2 && cn <= 32) warp_tiny_ksort(Y, A, cs, cn, wk, wseg);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // E: scatter into the other buffer; new segment starts travel with the keys.
-#pragma unroll
-    for (int j = 0; j < JMAX; ++j) {
-      if (j < J) {
-        const int e = j * BLOCK + tid;
-        if (e < m) {
-          const int s = s0[e];
-          const int L = slot[s];
-          const int rl = (int)(sh.cnt[j * NW + w] + __popc(bal[j] & lt) - ps[j]);
-          const bool lf = (bal[j] >> lane) & 1u;
-          int d, ns;
-          if (e == s) {
-            d = s + L;
-            ns = d;
-          } else if (lf) {
-            d = s + rl;
-            ns = s;
-          } else {
-            d = s + L + 1 + ((e - s - 1) - rl);
-            ns = s + L + 1;
+    while (true) {
+      unsigned long long e = 0;
+      if (lane == 0) e = small_pop(q);
+      e = __shfl_sync(kFull, e, 0);
+      if (e == 0ull) break;
+      int s = (int)(e >> 32), n = (int)((e >> 1) & 0x7fffffffu), par = (int)(e & 1ull);
+      while (true) {
+        const K *X = par ? B : A;
+        K *Y = par ? A : B;
+        ++nseg;
+        const K key = X[s];  // Step 1
+        const int L = warp_partition(X, Y, s, n, key);
+        if (lane == 0) A[s + L] = key;  // Step 4: final index
+        const int ls = s, ln = L, rs = s + L + 1, rn = n - L - 1, cp = par ^ 1;
+        if (cp && ln == 1 && lane == 0) A[ls] = Y[ls];
+        if (cp && rn == 1 && lane == 0) A[rs] = Y[rs];
+        if (ln >= 2 && ln <= 32) warp_tiny_ksort(Y, A, ls, ln, wk, wseg);
+        if (rn >= 2 && rn <= 32) warp_tiny_ksort(Y, A, rs, rn, wk, wseg);
+        __syncwarp();
+        const bool bl = ln > 32, br = rn > 32;
+        if (bl && br) {  // Steps 5-6: queue the smaller side, keep the larger
+          if (lane == 0) {
+            if (ln < rn) small_push(q, ls, ln, cp);
+            else small_push(q, rs, rn, cp);
           }
-          if ((unsigned)d < (unsigned)m) {
-            k1[d] = k0[e];
-            s1[d] = (unsigned short)ns;
-          } else {
-            sh.bad = 1;
-          }
-          if (e == m - 1 || s0[e + 1] != s) {
-            const int size = e - s + 1;
-            if (L >= 2 || size - L - 1 >= 2) sh.next_active = 1;
-          }
+          if (ln < rn) { s = rs; n = rn; } else { s = ls; n = ln; }
+          par = cp;
+        } else if (bl) {
+          s = ls; n = ln; par = cp;
+        } else if (br) {
+          s = rs; n = rn; par = cp;
+        } else {
+          break;
         }
       }
+      if (lane == 0) {
+        __threadfence_block();
+        atomicSub(&q.pending, 1);
+      }
     }
-    __syncthreads();
-    K *tk = k0; k0 = k1; k1 = tk;
-    unsigned short *ts = s0; s0 = s1; s1 = ts;
-    if (tid == 0) sh.active = sh.next_active;
-    __syncthreads();
   }
   __syncthreads();
-  for (int e = tid; e < m; e += BLOCK) out[e] = k0[e];
-  if (tid == 0) *levels += nlev;
-  return sh.bad == 0;
+  copy_out<K, BLOCK>(A, out, (unsigned)m);
+  if (tid == 0) *segments += nseg;
+  return q.bad == 0;
 }
 
 // ----------------------------------------------------------------------------- queue
+// Work items live in a bump-allocated pool. The sort runs in two phases.
+// Phase 1 (Steps 1-4 on items above the cutoff, with Steps 5-6 queuing their sides):
+// a large item reserves one ticket per tile pass; tickets index both the look-back
+// descriptors and a ticket map that names the item. CTAs claim tickets with one
+// atomicAdd, in order, possibly before the item that owns the ticket exists; they then
+// wait for it, so a freshly queued item starts without any dispatch delay. Phase 2
+// starts when every large item has completed: the small items, now a complete list,
+// are claimed with atomicAdd and finished in shared memory. Entries carry the sort's
+// epoch, so no memset is needed between sorts.
+__device__ __forceinline__ unsigned long long q_entry(unsigned epoch, unsigned long long idx) {
+  return ((unsigned long long)epoch << 32) | idx;
+}
+
 template <typename K, int TILE>
 __device__ __forceinline__ bool push_item(const SortParams &p, unsigned epoch, long long b,
                                           long long e, unsigned parity) {
@@ -503,10 +674,10 @@ __device__ __forceinline__ bool push_item(const SortParams &p, unsigned epoch, l
   const K *buf = parity ? static_cast<const K *>(p.scratch) : static_cast<const K *>(p.keys);
   const bool small = m <= p.cutoff;
   const unsigned tiles = small ? 1u : tile_count<K, TILE>(buf, b, e);
-  unsigned long long lbi = 0;
+  unsigned long long t0 = 0;
   if (!small) {
-    lbi = atomicAdd(&ctl->lb_used, (unsigned long long)tiles);
-    if (lbi + tiles > p.lb_cap) {
+    t0 = atomicAdd(&ctl->lb_used, (unsigned long long)tiles);
+    if (t0 + tiles > p.lb_cap) {
       raise_error(ctl, &ctl->abort, kDevWorkspaceExhausted, 2);
       return false;
     }
@@ -520,184 +691,244 @@ __device__ __forceinline__ bool push_item(const SortParams &p, unsigned epoch, l
   it->begin = b;
   it->end = e;
   it->tiles = tiles;
-  it->lb = (unsigned)lbi;
+  it->lb = (unsigned)t0;
   it->flags = (parity ? kItemScratch : 0u) | (small ? kItemSmall : 0u);
-  ItemCtl *c = p.ictl + idx;
-  c->grab = 0;
-  c->done = 0;
-  c->less = 0;
-  __threadfence();
-  st_release(&it->ready, epoch);
+  it->epoch = epoch;
+  if (small) {
+    __threadfence();
+    const unsigned long long qi = atomicAdd(&ctl->sq_tail, 1ull);  // qi <= idx < item_cap
+    st_release(&p.small_q[qi], q_entry(epoch, idx));
+  } else {
+    ItemCtl *c = p.ictl + idx;
+    c->done = 0;
+    c->less = 0;
+    atomicAdd(&ctl->large_pushed, 1ull);
+    __threadfence();
+    const unsigned long long entry = q_entry(epoch, idx);
+    for (unsigned j = 0; j < tiles; ++j) st_relaxed(&p.tmap[t0 + j], entry);
+  }
   return true;
 }
 
-// Thread 0 of a CTA: claim the next tile (or small item). Returns false when the
-// queue has drained or the call was aborted.
-__device__ __forceinline__ bool fetch_work(const SortParams &p, unsigned epoch, long long *h_out,
+__device__ __forceinline__ void load_item(const Item *ip, Item *it) {
+  it->begin = __ldcg(&ip->begin);
+  it->end = __ldcg(&ip->end);
+  it->tiles = __ldcg(&ip->tiles);
+  it->lb = __ldcg(&ip->lb);
+  it->flags = __ldcg(&ip->flags);
+  it->epoch = 0;
+}
+
+// Thread 0 of a CTA, phase 1: waits for ticket k to be issued. Returns 1 with the
+// item, 0 when phase 1 is over (every large item completed), -1 on abort or timeout.
+__device__ __forceinline__ int wait_ticket(const SortParams &p, unsigned epoch,
+                                           unsigned long long k, long long *h_out,
                                            unsigned *t_out, Item *it_out) {
   Control *ctl = p.ctl;
-  unsigned ns = 32;
-  unsigned long long idle_t0 = 0, last_completed = ~0ull;
+  unsigned ns = 16;
+  unsigned long long idle_t0 = 0, last = ~0ull;
   while (true) {
-    if (ld_relaxed(&ctl->abort)) return false;
-    const unsigned long long h = ld_relaxed(&ctl->head);
-    const unsigned long long tail = ld_acquire(&ctl->pushed);
-    if (h < tail && h < p.item_cap) {
-      Item *ip = p.items + h;
-      unsigned spins = 0;
-      unsigned long long t0 = 0;
-      while (ld_acquire(&ip->ready) != epoch) {
-        if ((++spins & 255u) == 0u) {
-          const unsigned long long now = globaltimer();
-          if (t0 == 0) t0 = now;
-          if (now - t0 > p.spin_limit_ns) {
-            raise_error(ctl, &ctl->abort, kDevTimeout, 0x200000000ull | h);
-            return false;
-          }
-          if (ld_relaxed(&ctl->abort)) return false;
-        }
-        __nanosleep(32);
+    if (k < p.lb_cap) {
+      const unsigned long long v = ld_acquire(&p.tmap[k]);
+      if ((unsigned)(v >> 32) == epoch) {
+        const long long idx = (long long)(v & 0xffffffffull);
+        load_item(p.items + idx, it_out);
+        *h_out = idx;
+        *t_out = (unsigned)(k - it_out->lb);
+        return 1;
       }
-      Item it;
-      it.begin = __ldcg(&ip->begin);
-      it.end = __ldcg(&ip->end);
-      it.tiles = __ldcg(&ip->tiles);
-      it.lb = __ldcg(&ip->lb);
-      it.flags = __ldcg(&ip->flags);
-      it.ready = epoch;
-      const unsigned t = atomicAdd(&p.ictl[h].grab, 1u);
-      if (t < it.tiles) {
-        *h_out = (long long)h;
-        *t_out = t;
-        *it_out = it;
-        return true;
-      }
-      atomicCAS(&ctl->head, h, h + 1);
-      ns = 32;
-      continue;
     }
-    // Nothing visible: finished when every pushed item has completed. `completed` is
-    // read before `pushed`: items push their children before they count as completed.
-    const unsigned long long c = ld_acquire(&ctl->completed);
-    const unsigned long long pu = ld_acquire(&ctl->pushed);
-    if (c == pu) return false;
+    if (ld_relaxed(&ctl->abort)) return -1;
+    // `completed` before `pushed`: an item queues its sides before it completes
+    const unsigned long long c = ld_acquire(&ctl->large_completed);
+    const unsigned long long pu = ld_acquire(&ctl->large_pushed);
+    if (c == pu) return 0;
     const unsigned long long now = globaltimer();
-    if (c != last_completed) {
-      last_completed = c;
+    if (c != last) {
+      last = c;
       idle_t0 = now;
     } else if (now - idle_t0 > p.spin_limit_ns) {
-      raise_error(ctl, &ctl->abort, kDevTimeout, 0x300000000ull | c);
-      return false;
+      raise_error(ctl, &ctl->abort, kDevTimeout, 0x300000000ull | k);
+      return -1;
     }
     __nanosleep(ns);
-    ns = ns < 1024 ? ns * 2 : 1024;
+    ns = ns < 256 ? ns * 2 : 256;
   }
 }
 
-template <int BLOCK, int JMAX>
+// Thread 0 of a CTA, phase 2: claims the next small item. Returns false when none is left.
+__device__ __forceinline__ bool claim_small(const SortParams &p, unsigned epoch, long long *h_out,
+                                            Item *it_out) {
+  Control *ctl = p.ctl;
+  if (ld_relaxed(&ctl->abort)) return false;
+  const unsigned long long j = atomicAdd(&ctl->sq_head, 1ull);
+  if (j >= ld_acquire(&ctl->sq_tail) || j >= p.item_cap) return false;
+  unsigned long long t0 = 0;
+  for (unsigned spins = 1;; ++spins) {  // queued before phase 2 began: already visible
+    const unsigned long long v = ld_acquire(&p.small_q[j]);
+    if ((unsigned)(v >> 32) == epoch) {
+      const long long idx = (long long)(v & 0xffffffffull);
+      load_item(p.items + idx, it_out);
+      *h_out = idx;
+      return true;
+    }
+    if ((spins & 255u) == 0u) {
+      const unsigned long long now = globaltimer();
+      if (t0 == 0) t0 = now;
+      if (now - t0 > p.spin_limit_ns) {
+        raise_error(ctl, &ctl->abort, kDevTimeout, 0x200000000ull | j);
+        return false;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+template <int BLOCK>
 struct SortShared {
   TileShared<BLOCK> tile;
-  SmemShared<BLOCK, JMAX> fin;
+  SmallShared small;
   long long h;
   unsigned t;
   int has_work;
-  int finisher;
   Item it;
 };
 
-// Persistent sort kernel: every CTA loops over the work queue until it drains.
-template <typename K, int BLOCK, int IPT, int JMAX>
-__global__ void __launch_bounds__(BLOCK) sort_kernel(SortParams p) {
+// Persistent sort kernel: phase 1 (tile passes of large items) then phase 2 (small
+// items), see the queue notes above.
+template <typename K, int BLOCK, int IPT, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) sort_kernel(SortParams p) {
   constexpr int TILE = BLOCK * IPT;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ SortShared<BLOCK, JMAX> sh;
+  __shared__ SortShared<BLOCK> sh;
   K *const buf0 = static_cast<K *>(p.keys);
   K *const buf1 = static_cast<K *>(p.scratch);
   Control *ctl = p.ctl;
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const int tid = threadIdx.x;
-  unsigned long long st_tiles = 0, st_lb = 0, st_levels = 0, st_small = 0, st_small_keys = 0;
+  unsigned long long st_tiles = 0, st_lb = 0, st_segs = 0, st_small = 0, st_small_keys = 0;
   unsigned long long st_large = 0, st_large_keys = 0;
+  unsigned long long cy_fetch = 0, cy_small = 0, cy_tile = 0, cy_fin = 0;
+  long long c0 = clock64();
+  bool aborted = false;
 
+  // ---- phase 1
   while (true) {
-    if (tid == 0) sh.has_work = fetch_work(p, epoch, &sh.h, &sh.t, &sh.it) ? 1 : 0;
+    if (tid == 0) {
+      const unsigned long long k = atomicAdd(&ctl->tq_head, 1ull);
+      sh.has_work = wait_ticket(p, epoch, k, &sh.h, &sh.t, &sh.it);
+    }
     __syncthreads();
-    if (!sh.has_work) break;
+    {
+      const long long c1 = clock64();
+      cy_fetch += (unsigned long long)(c1 - c0);
+      c0 = c1;
+    }
+    if (sh.has_work <= 0) {
+      aborted = sh.has_work < 0;
+      break;
+    }
     const Item it = sh.it;
     const long long h = sh.h;
     const unsigned t = sh.t;
     const unsigned par = it.flags & kItemScratch;
     K *src = par ? buf1 : buf0;
     K *dst = par ? buf0 : buf1;
-
-    if (it.flags & kItemSmall) {
-      const int m = (int)(it.end - it.begin);
-      const bool fin_ok = smem_ksort<K, BLOCK, JMAX>(src + it.begin, buf0 + it.begin, m,
-                                                     p.cutoff, smem, sh.fin, &st_levels);
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) {
-        if (!fin_ok) raise_error(ctl, &ctl->abort, kDevInternal, 0x600000000ull | (unsigned)h);
-        ++st_small;
-        st_small_keys += (unsigned long long)m;
-        atomicAdd(&ctl->completed, 1ull);
+    unsigned long long less = 0;
+    const bool ok = partition_tile<K, BLOCK, IPT>(
+        src, dst, it.begin, it.end, t, p.lb + it.lb, epoch, p.spin_limit_ns, ctl, &ctl->abort,
+        reinterpret_cast<K *>(smem), sh.tile, &less, &st_lb);
+    if (!ok) {
+      aborted = true;
+      break;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();  // release the CTA's tile writes (ordered before by the barrier)
+      {
+        const long long c1 = clock64();
+        cy_tile += (unsigned long long)(c1 - c0);
+        c0 = c1;
       }
-    } else {
-      unsigned long long less = 0;
-      const bool ok = partition_tile<K, BLOCK, IPT>(
-          src, dst, it.begin, it.end, t, p.lb + it.lb, epoch, p.spin_limit_ns, ctl, &ctl->abort,
-          reinterpret_cast<K *>(smem), sh.tile, &less, &st_lb);
-      if (!ok) break;
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) {
-        ++st_tiles;
-        if (t == it.tiles - 1) {
-          atomicExch(&p.ictl[h].less, less);
-          __threadfence();
-        }
-        const unsigned old = atomicAdd(&p.ictl[h].done, 1u);
-        sh.finisher = old == it.tiles - 1;
-        if (sh.finisher) {
-          __threadfence();
-          // Step 4: the key goes to its final index; Steps 5-6: both sides are queued.
-          const unsigned long long c = ld_acquire(&p.ictl[h].less);
-          const K key = __ldcg(src + it.begin);
-          const long long kpos = it.begin + (long long)c;
-          if (kpos >= it.end) {
-            raise_error(ctl, &ctl->abort, kDevInternal, 0x700000000ull | (unsigned)h);
-          } else {
-            buf0[kpos] = key;
-            const unsigned cpar = par ^ 1u;
-            const long long cb[2] = {it.begin, kpos + 1};
-            const long long ce[2] = {kpos, it.end};
+      ++st_tiles;
+      if (t == it.tiles - 1) {
+        atomicExch(&p.ictl[h].less, less);
+        __threadfence();
+      }
+      const unsigned old = atomicAdd(&p.ictl[h].done, 1u);
+      if (old == it.tiles - 1) {
+        __threadfence();
+        // Step 4: the key goes to its final index; Steps 5-6: both sides are queued.
+        const unsigned long long c = ld_acquire(&p.ictl[h].less);
+        const K key = __ldcg(src + it.begin);
+        const long long kpos = it.begin + (long long)c;
+        if (kpos >= it.end) {
+          raise_error(ctl, &ctl->abort, kDevInternal, 0x700000000ull | (unsigned)h);
+        } else {
+          buf0[kpos] = key;
+          const unsigned cpar = par ^ 1u;
+          const long long cb[2] = {it.begin, kpos + 1};
+          const long long ce[2] = {kpos, it.end};
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-              const long long m = ce[s] - cb[s];
-              if (m == 1) {
-                if (cpar) buf0[cb[s]] = __ldcg(dst + cb[s]);
-              } else if (m >= 2) {
-                push_item<K, TILE>(p, epoch, cb[s], ce[s], cpar);
-              }
+          for (int s = 0; s < 2; ++s) {
+            const long long m = ce[s] - cb[s];
+            if (m == 1) {
+              if (cpar) buf0[cb[s]] = __ldcg(dst + cb[s]);
+            } else if (m >= 2) {
+              push_item<K, TILE>(p, epoch, cb[s], ce[s], cpar);
             }
           }
-          ++st_large;
-          st_large_keys += (unsigned long long)(it.end - it.begin);
-          __threadfence();
-          atomicAdd(&ctl->completed, 1ull);
         }
+        ++st_large;
+        st_large_keys += (unsigned long long)(it.end - it.begin);
+        __threadfence();
+        atomicAdd(&ctl->large_completed, 1ull);
       }
+      const long long c1 = clock64();
+      cy_fin += (unsigned long long)(c1 - c0);
+      c0 = c1;
     }
     __syncthreads();
   }
+
+  // ---- phase 2
+  while (!aborted) {
+    if (tid == 0) sh.has_work = claim_small(p, epoch, &sh.h, &sh.it) ? 1 : 0;
+    __syncthreads();
+    {
+      const long long c1 = clock64();
+      cy_fetch += (unsigned long long)(c1 - c0);
+      c0 = c1;
+    }
+    if (!sh.has_work) break;
+    const Item it = sh.it;
+    const K *src = (it.flags & kItemScratch) ? buf1 : buf0;
+    const int m = (int)(it.end - it.begin);
+    const bool fin_ok = smem_ksort<K, BLOCK>(src + it.begin, buf0 + it.begin, m, p.cutoff, smem,
+                                             sh.small, &st_segs);
+    __syncthreads();
+    if (tid == 0) {
+      if (!fin_ok) raise_error(ctl, &ctl->abort, kDevInternal, 0x600000000ull | (unsigned)sh.h);
+      ++st_small;
+      st_small_keys += (unsigned long long)m;
+      const long long c1 = clock64();
+      cy_small += (unsigned long long)(c1 - c0);
+      c0 = c1;
+    }
+  }
+
   if (tid == 0) {
     if (st_tiles) atomicAdd(&ctl->tiles, st_tiles);
     if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
-    if (st_levels) atomicAdd(&ctl->smem_levels, st_levels);
+    if (st_segs) atomicAdd(&ctl->smem_levels, st_segs);
     if (st_small) atomicAdd(&ctl->small_items, st_small);
     if (st_small_keys) atomicAdd(&ctl->small_keys, st_small_keys);
     if (st_large) atomicAdd(&ctl->large_items, st_large);
     if (st_large_keys) atomicAdd(&ctl->large_keys, st_large_keys);
+    atomicAdd(&ctl->cyc_fetch, cy_fetch);
+    atomicAdd(&ctl->cyc_small, cy_small);
+    atomicAdd(&ctl->cyc_tile, cy_tile);
+    atomicAdd(&ctl->cyc_finish, cy_fin);
   }
 }
 
@@ -711,13 +942,15 @@ __global__ void seed_kernel(SortParams p) {
     if (ep == 0u || ep >= kPartitionEpoch) ep = 1u;
     ctl->epoch = ep;
     ctl->pushed = 0;
-    ctl->completed = 0;
-    ctl->head = 0;
+    ctl->large_pushed = ctl->large_completed = 0;
+    ctl->tq_head = 0;
+    ctl->sq_head = ctl->sq_tail = 0;
     ctl->lb_used = 0;
     ctl->abort = 0;
     ctl->large_items = ctl->large_keys = ctl->tiles = 0;
     ctl->small_items = ctl->small_keys = 0;
     ctl->smem_levels = ctl->lookback_steps = 0;
+    ctl->cyc_fetch = ctl->cyc_small = ctl->cyc_tile = ctl->cyc_finish = 0;
     epoch_sh = ep;
   }
   __syncthreads();
@@ -768,9 +1001,9 @@ __global__ void __launch_bounds__(BLOCK) partition_kernel(PartParams p) {
   } else if (threadIdx.x == 0) {
     raise_error(p.ctl, &pc->abort, kDevInternal, 0x800000000ull | t);
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();  // release the CTA's tile writes (ordered before by the barrier)
     if (ok && t == ntiles - 1) {
       atomicExch(&pc->less, less);
       __threadfence();

@@ -31,10 +31,12 @@ constexpr long long kMaxItemKeys = 0x7fffffffLL;
 // Per-workspace control block (device memory). The dispatch fields are reset by the
 // seed kernel at every sort; `error` is sticky until the host reads it.
 struct alignas(128) Control {
-  unsigned long long pushed;     // work-queue slots handed out
-  unsigned long long completed;  // work items finished
-  unsigned long long head;       // dispatch cursor
-  unsigned long long lb_used;    // look-back descriptors handed out
+  unsigned long long pushed;           // work items allocated in the pool
+  unsigned long long large_pushed;     // large items queued
+  unsigned long long large_completed;  // large items fully partitioned
+  unsigned long long tq_head;          // tile tickets claimed by CTAs
+  unsigned long long lb_used;          // tile tickets (= look-back descriptors) issued
+  unsigned long long sq_head, sq_tail; // small-item list: claimed, queued
   unsigned epoch;                // generation of the current sort (never 0)
   unsigned abort;                // nonzero: stop the current call early
   unsigned error;                // first device error since the host last read it
@@ -43,6 +45,8 @@ struct alignas(128) Control {
   // statistics of the last sort
   unsigned long long large_items, large_keys, tiles, small_items, small_keys;
   unsigned long long smem_levels, lookback_steps;
+  // SM cycles spent by the CTAs of the sort kernel, by phase (sum over CTAs)
+  unsigned long long cyc_fetch, cyc_small, cyc_tile, cyc_finish;
   unsigned long long pad1[3];
 };
 
@@ -53,7 +57,7 @@ struct alignas(32) Item {
   unsigned tiles;   // tile passes of a large item; 1 for a small item
   unsigned lb;      // first look-back descriptor of a large item
   unsigned flags;   // kItemScratch | kItemSmall
-  unsigned ready;   // equals Control::epoch once the item is published
+  unsigned epoch;   // generation of the sort that wrote the item
 };
 
 struct alignas(16) ItemCtl {
@@ -82,8 +86,10 @@ struct SortParams {
   Control *ctl;
   Item *items;
   ItemCtl *ictl;
+  unsigned long long *small_q;  // item_cap entries: (epoch << 32) | item index
   unsigned long long item_cap;
-  unsigned long long *lb;
+  unsigned long long *lb;       // lb_cap look-back descriptors, one per tile ticket
+  unsigned long long *tmap;     // lb_cap entries: (epoch << 32) | item of the ticket
   unsigned long long lb_cap;
   const long long *offsets;  // roots: offsets[r] .. offsets[r+1]; null = one root [0, n)
   long long num_roots;
@@ -108,7 +114,7 @@ struct PartParams {
 struct KernelInfo {
   int block;          // threads per CTA
   int tile_keys;      // keys per tile pass
-  int max_cutoff;     // largest shared-memory item the kernel is built for
+  int max_cutoff;     // largest shared-memory item the kernel supports
 };
 
 template <typename K>

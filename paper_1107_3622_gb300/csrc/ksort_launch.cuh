@@ -7,23 +7,30 @@
 namespace ksort {
 
 // Compile-time shape of the kernels for a key type: threads per CTA, keys per thread
-// in a tile pass, and the largest shared-memory item (JMAX chunks of BLOCK keys).
+// in a tile pass, the CTAs per SM the register budget is sized for, and the largest
+// shared-memory item.
 template <typename K> struct Shape;
-template <> struct Shape<float> { static constexpr int BLOCK = 512, IPT = 16, JMAX = 8; };
-template <> struct Shape<unsigned> { static constexpr int BLOCK = 512, IPT = 16, JMAX = 8; };
-template <> struct Shape<double> { static constexpr int BLOCK = 512, IPT = 8, JMAX = 8; };
+template <> struct Shape<float> {
+  static constexpr int BLOCK = 256, IPT = 16, MINB = 4, MAX_CUTOFF = dev::kMaxSmallCutoff;
+};
+template <> struct Shape<unsigned> {
+  static constexpr int BLOCK = 256, IPT = 16, MINB = 4, MAX_CUTOFF = dev::kMaxSmallCutoff;
+};
+template <> struct Shape<double> {
+  static constexpr int BLOCK = 256, IPT = 8, MINB = 4, MAX_CUTOFF = 8192;
+};
 
 template <typename K>
 KernelInfo Launcher<K>::info() {
   using S = Shape<K>;
-  return KernelInfo{S::BLOCK, S::BLOCK * S::IPT, S::BLOCK * S::JMAX};
+  return KernelInfo{S::BLOCK, S::BLOCK * S::IPT, S::MAX_CUTOFF};
 }
 
 template <typename K>
 size_t Launcher<K>::sort_smem_bytes(int cutoff) {
   using S = Shape<K>;
-  const size_t stage = (size_t)S::BLOCK * S::IPT * sizeof(K);
-  const size_t fin = dev::smem_finisher_bytes<K>(cutoff);
+  const size_t stage = (size_t)2 * S::BLOCK * S::IPT * sizeof(K);
+  const size_t fin = dev::smem_finisher_bytes<K>(cutoff, S::BLOCK / 32);
   return stage > fin ? stage : fin;
 }
 
@@ -36,7 +43,7 @@ long long Launcher<K>::tile_count(const void *buf, long long begin, long long en
 template <typename K>
 cudaError_t Launcher<K>::max_ctas_per_sm(int cutoff, int *out) {
   using S = Shape<K>;
-  auto kern = dev::sort_kernel<K, S::BLOCK, S::IPT, S::JMAX>;
+  auto kern = dev::sort_kernel<K, S::BLOCK, S::IPT, S::MINB>;
   const size_t smem = sort_smem_bytes(cutoff);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -47,7 +54,7 @@ template <typename K>
 cudaError_t Launcher<K>::partition_out(const PartParams &p, int num_tiles, cudaStream_t s) {
   using S = Shape<K>;
   auto kern = dev::partition_kernel<K, S::BLOCK, S::IPT>;
-  const size_t smem = (size_t)S::BLOCK * S::IPT * sizeof(K);
+  const size_t smem = (size_t)2 * S::BLOCK * S::IPT * sizeof(K);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<num_tiles, S::BLOCK, smem, s>>>(p);
@@ -64,7 +71,7 @@ cudaError_t Launcher<K>::seed(const SortParams &p, cudaStream_t s) {
 template <typename K>
 cudaError_t Launcher<K>::sort(const SortParams &p, int grid, cudaStream_t s) {
   using S = Shape<K>;
-  auto kern = dev::sort_kernel<K, S::BLOCK, S::IPT, S::JMAX>;
+  auto kern = dev::sort_kernel<K, S::BLOCK, S::IPT, S::MINB>;
   const size_t smem = sort_smem_bytes(p.cutoff);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
