@@ -49,7 +49,8 @@ PAPER_KEYS_PER_S = N_KEYS / PAPER_KSORT_S_AT_7E6
 L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = "ksort_sort n=7e6 float32 U[0,1] (Table 1 size)"
 DEVICE_SOURCES = ("paper_1107_3622_gb300/csrc/ksort_device.cuh",
-                  "paper_1107_3622_gb300/csrc/ksort_launch.cuh")
+                  "paper_1107_3622_gb300/csrc/ksort_launch.cuh",
+                  "paper_1107_3622_gb300/csrc/ksort_internal.h")
 
 
 def parse_args(argv=None):
@@ -327,8 +328,9 @@ def run_ours(args, dist: Dist):
     achieved = algo_bytes / (ms_mean / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
-                "traffic": recorded_traffic("sort_kernel<float>", WORKLOAD),
-                "kernel": "ksort_sort (1-CTA seed + persistent sort_kernel<float>)",
+                "traffic": recorded_traffic("ksort_sort<float>", WORKLOAD),
+                "kernel": "ksort_sort: seed_kernel + tile_kernel<float> (tile passes) + "
+                          "small_kernel<float> (shared-memory finisher), one call",
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "lower_bound_bytes": 2 * 4 * n,
                 "lower_bound_frac": round((2 * 4 * n) / (ms_mean / 1e3) / 1e9 / peak, 5)}
@@ -421,10 +423,11 @@ def run_partition_pass(ks, n, peak, peak_src):
     o = outs[0]
     assert float(o[i]) == float(ins[0][0])
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
-    return {"kernel": "partition_kernel<float>", "n": n, "us_per_launch": round(ms * 1e3, 2),
+    return {"kernel": "ksort_partition_out: seed_kernel + tile_kernel<float>", "n": n,
+            "us_per_launch": round(ms * 1e3, 2),
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),
             "peak_source": f"{peak_src} hbm_gbs",
-            "traffic": recorded_traffic("partition_kernel<float>", f"n={n} f32 rotating 8 buffers"),
+            "traffic": recorded_traffic("tile_kernel<float>", f"n={n} f32 rotating 8 buffers"),
             "algorithmic_bytes_per_launch": 8 * n,
             "method": f"{R} buffer pairs ({2 * R * 4 * n >> 20} MiB) rotated, {reps} rounds, "
                       "CUDA events around back-to-back launches"}

@@ -111,10 +111,6 @@ typedef struct {
     uint64_t smem_levels;   /* partition levels run inside shared memory (all items)   */
     uint64_t lookback_steps;/* 32-wide look-back windows examined                      */
     uint64_t items_pushed;  /* work-queue entries used                                 */
-    uint64_t cycles_fetch;  /* SM cycles of the sort kernel's CTAs (summed) spent       */
-    uint64_t cycles_small;  /*   waiting for / claiming work, finishing small items,    */
-    uint64_t cycles_tiles;  /*   running tile passes, and placing keys / queueing the   */
-    uint64_t cycles_finish; /*   two sides (Step 4 and Steps 5-6)                       */
 } ksort_stats_t;
 KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out);
 
@@ -141,6 +137,15 @@ KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
  * records KSORT_ERR_TIMEOUT in the stream's workspace and returns; the next
  * ksort_get_device_error(stream) reports it. No fault, trap or endless loop. */
 KSORT_API ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stream);
+
+/* Diagnostics: while set, every tile pass of ksort_sort / ksort_sort_batched /
+ * ksort_partition* writes 8 uint64 words per tile ticket into trace_dev[ticket * 8 ..]
+ * for tickets < `tickets`: %globaltimer stamps (ns) of [0] ticket claimed, [1] ticket
+ * issued, [2] keys loaded and counted, [3] look-back done, [4] written, [5] first
+ * look-back window read (0 for tile 0), [6] completed; [7] = CTA index
+ * | look-back windows << 20 | look-back polls << 40. The caller owns the buffer
+ * (device memory); pass NULL / 0 to stop. Costs a little time. */
+KSORT_API ksort_status_t ksort_debug_trace(uint64_t *trace_dev, int64_t tickets);
 
 /* Static text for a status code. */
 KSORT_API const char *ksort_status_string(ksort_status_t status);

@@ -22,7 +22,7 @@ __all__ = [
     "ksort_reserve_workspace", "ksort_release_workspace", "ksort_get_device_error",
     "ksort_get_stats", "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
     "ksort_tile_keys", "ksort_status_string", "ksort_last_cuda_error",
-    "ksort_selftest_wait_timeout",
+    "ksort_selftest_wait_timeout", "ksort_debug_trace",
     "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
 ]
 
@@ -30,7 +30,8 @@ F32, F64, U32 = 0, 1, 2
 _NAMES = {F32: "f32", F64: "f64", U32: "u32"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "_lib", "libksort.so")
+# KSORT_LIBRARY may name another build of the same sources (used for tuning sweeps).
+_LIB_PATH = os.environ.get("KSORT_LIBRARY") or os.path.join(_HERE, "_lib", "libksort.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -47,8 +48,7 @@ class KSortError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "large_items", "large_keys", "tiles", "small_items", "small_keys",
-        "smem_levels", "lookback_steps", "items_pushed", "cycles_fetch", "cycles_small",
-        "cycles_tiles", "cycles_finish")]
+        "smem_levels", "lookback_steps", "items_pushed")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -72,7 +72,7 @@ def load():
         if _lib is not None:
             return _lib
         from . import _build
-        if not _build.up_to_date():
+        if not os.environ.get("KSORT_LIBRARY") and not _build.up_to_date():
             try:
                 _build.build()
             except Exception as e:  # no toolkit: fail loudly, never fall back
@@ -97,6 +97,7 @@ def load():
             "ksort_status_string": (ctypes.c_char_p, [i32]),
             "ksort_last_cuda_error": (ctypes.c_char_p, []),
             "ksort_selftest_wait_timeout": (i32, [i32, vp]),
+            "ksort_debug_trace": (i32, [vp, i64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -215,6 +216,12 @@ def ksort_tile_keys(dtype: int) -> int:
 def ksort_selftest_wait_timeout(limit_ms: int, stream=None):
     _check(load().ksort_selftest_wait_timeout(limit_ms, _stream(stream)),
            "ksort_selftest_wait_timeout")
+
+
+def ksort_debug_trace(trace=None, tickets: int = 0):
+    """Installs (or with None removes) a device uint64 buffer of 8 * tickets timestamps."""
+    _check(load().ksort_debug_trace(_ptr(trace) if trace is not None else None,
+                                    tickets if trace is not None else 0), "ksort_debug_trace")
 
 
 def ksort_status_string(status: int) -> str:

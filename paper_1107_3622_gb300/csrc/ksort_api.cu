@@ -36,19 +36,18 @@ bool dtype_ok(int dt) { return dt == KSORT_F32 || dt == KSORT_F64 || dt == KSORT
 // ------------------------------------------------------------------ per-type dispatch
 struct Ops {
   KernelInfo (*info)();
-  size_t (*sort_smem_bytes)(int);
-  cudaError_t (*max_ctas_per_sm)(int, int *);
-  cudaError_t (*partition_out)(const PartParams &, int, cudaStream_t);
+  size_t (*small_smem_bytes)(int);
+  cudaError_t (*occupancy)(int, int *, int *);
   cudaError_t (*seed)(const SortParams &, cudaStream_t);
-  cudaError_t (*sort)(const SortParams &, int, cudaStream_t);
+  cudaError_t (*tiles)(const SortParams &, int, cudaStream_t);
+  cudaError_t (*smalls)(const SortParams &, int, cudaStream_t);
   long long (*tile_count)(const void *, long long, long long);
 };
 
 template <typename K>
 Ops ops_for() {
-  return Ops{&Launcher<K>::info,          &Launcher<K>::sort_smem_bytes,
-             &Launcher<K>::max_ctas_per_sm, &Launcher<K>::partition_out,
-             &Launcher<K>::seed,          &Launcher<K>::sort,
+  return Ops{&Launcher<K>::info,   &Launcher<K>::small_smem_bytes, &Launcher<K>::occupancy,
+             &Launcher<K>::seed,   &Launcher<K>::tiles,            &Launcher<K>::smalls,
              &Launcher<K>::tile_count};
 }
 
@@ -65,14 +64,15 @@ struct Tuning {
 };
 
 std::mutex g_mu;
-Tuning g_tuning[3] = {{8192, 0, 2000}, {4096, 0, 2000}, {8192, 0, 2000}};
+unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
+long long g_trace_cap = 0;
+Tuning g_tuning[3] = {{4096, 0, 2000}, {2048, 0, 2000}, {4096, 0, 2000}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
   void *base = nullptr;
   size_t bytes = 0;
   Control *ctl = nullptr;
-  PartCtl *pctl = nullptr;
   unsigned long long *lb = nullptr;
   unsigned long long lb_cap = 0;
   Item *items = nullptr;
@@ -87,6 +87,9 @@ struct Workspace {
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bytes past the scratch keys that bulk copies of whole 16-byte chunks may read.
+constexpr size_t kScratchPad = 64;
 
 struct Need {
   unsigned long long item_cap, lb_cap;
@@ -131,12 +134,10 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
     KS_CUDA(cudaFree(ws.base));
     ws.base = nullptr;
   }
-  // [Control][PartCtl][look-back][items][item counters][scratch keys]
+  // [Control][look-back][items][item counters][ticket map][small list][scratch keys]
   size_t off = 0;
   const size_t o_ctl = off;
   off = align_up(off + sizeof(Control), 256);
-  const size_t o_pctl = off;
-  off = align_up(off + sizeof(PartCtl), 256);
   const size_t o_lb = off;
   off = align_up(off + lb_cap * sizeof(unsigned long long), 256);
   const size_t o_items = off;
@@ -149,7 +150,7 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   off = align_up(off + item_cap * sizeof(unsigned long long), 256);
   const size_t meta = off;
   const size_t o_scr = off;
-  off = align_up(off + scratch_bytes, 256);
+  off = align_up(off + scratch_bytes + kScratchPad, 256);
 
   void *base = nullptr;
   cudaError_t e = cudaMalloc(&base, off);
@@ -165,7 +166,6 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   ws.base = base;
   ws.bytes = off;
   ws.ctl = reinterpret_cast<Control *>(b + o_ctl);
-  ws.pctl = reinterpret_cast<PartCtl *>(b + o_pctl);
   ws.lb = reinterpret_cast<unsigned long long *>(b + o_lb);
   ws.lb_cap = lb_cap;
   ws.items = reinterpret_cast<Item *>(b + o_items);
@@ -206,24 +206,30 @@ ksort_status_t device_sms(int dev, int *sms) {
   return KSORT_OK;
 }
 
-std::map<std::pair<int, int>, int> g_occ;  // (dtype, cutoff) -> CTAs per SM
+struct Grids {
+  int tiles;   // tile_kernel CTAs filling the GPU
+  int smalls;  // small_kernel CTAs filling the GPU
+};
+std::map<std::pair<int, int>, std::pair<int, int>> g_occ;  // (dtype, cutoff) -> CTAs per SM
 
-ksort_status_t full_grid(ksort_dtype_t dt, int dev, const Tuning &tu, int *grid) {
+ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g) {
   int sms = 0;
   ksort_status_t st = device_sms(dev, &sms);
   if (st != KSORT_OK) return st;
   auto key = std::make_pair((int)dt, tu.cutoff);
   auto it = g_occ.find(key);
-  int occ = 0;
+  std::pair<int, int> occ;
   if (it == g_occ.end()) {
-    KS_CUDA(ops(dt).max_ctas_per_sm(tu.cutoff, &occ));
+    KS_CUDA(ops(dt).occupancy(tu.cutoff, &occ.first, &occ.second));
     g_occ[key] = occ;
   } else {
     occ = it->second;
   }
-  if (occ < 1) return KSORT_ERR_INTERNAL;
-  if (tu.ctas_per_sm > 0) occ = std::min(occ, tu.ctas_per_sm);
-  *grid = sms * occ;
+  if (occ.first < 1 || occ.second < 1) return KSORT_ERR_INTERNAL;
+  int small_occ = occ.second;
+  if (tu.ctas_per_sm > 0) small_occ = std::min(small_occ, tu.ctas_per_sm);
+  g->tiles = sms * occ.first;
+  g->smalls = sms * small_occ;
   return KSORT_OK;
 }
 
@@ -241,6 +247,8 @@ SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
   p.lb_cap = ws.lb_cap;
   p.cutoff = tu.cutoff;
   p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
+  p.trace = g_trace;
+  p.trace_cap = g_trace_cap;
   return p;
 }
 
@@ -278,18 +286,22 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
     if (!in_place) KS_CUDA(cudaMemcpyAsync(dst, in, kb, cudaMemcpyDeviceToDevice, s));
     return KSORT_OK;
   }
+  // One item that only runs Steps 1-4: buffer 0 is read, buffer 1 receives the result.
   const long long tiles = ops(dt).tile_count(in, 0, n);
-  if ((unsigned long long)tiles > ws->lb_cap || tiles > 0x7fffffffLL) return KSORT_ERR_INVALID_ARG;
-  PartParams p{};
-  p.in = in;
-  p.out = dst;
-  p.n = n;
+  if ((unsigned long long)tiles > ws->lb_cap) return KSORT_ERR_INVALID_ARG;
+  Grids g{};
+  if ((st = full_grids(dt, dev, tu, &g)) != KSORT_OK) return st;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(g.tiles, tiles));
+  SortParams p = sort_params(*ws, const_cast<void *>(in), tu);
+  p.scratch = dst;
+  p.num_roots = 1;
+  p.total = n;
+  p.root_flags = kItemPartitionOnly;
   p.key_index = reinterpret_cast<long long *>(key_index);
-  p.pctl = ws->pctl;
-  p.lb = ws->lb;
-  p.ctl = ws->ctl;
-  p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
-  KS_CUDA(ops(dt).partition_out(p, (int)tiles, s));
+  p.readable[0] = n;
+  p.readable[1] = 0;  // buffer 1 is only written
+  KS_CUDA(ops(dt).seed(p, s));
+  KS_CUDA(ops(dt).tiles(p, grid, s));
   if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
   return KSORT_OK;
 }
@@ -311,29 +323,34 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
   Workspace *ws = nullptr;
   st = get_workspace(dev, s, need_for(dt, total, num_arrays), &ws);
   if (st != KSORT_OK) return st;
-  int grid = 0;
-  if ((st = full_grid(dt, dev, tu, &grid)) != KSORT_OK) return st;
+  Grids g{};
+  if ((st = full_grids(dt, dev, tu, &g)) != KSORT_OK) return st;
   if (!offsets) {
+    // one array: no more CTAs than its first level has tiles, or than small items
     const KernelInfo ki = ops(dt).info();
-    const long long want = std::max<long long>((total + ki.tile_keys - 1) / ki.tile_keys,
-                                               2 * ((total + tu.cutoff - 1) / tu.cutoff));
-    grid = (int)std::max<long long>(1, std::min<long long>(grid, want));
+    g.tiles = (int)std::max<long long>(
+        1, std::min<long long>(g.tiles, (total + ki.tile_keys - 1) / ki.tile_keys));
+    g.smalls = (int)std::max<long long>(
+        1, std::min<long long>(g.smalls, 2 * ((total + tu.cutoff - 1) / tu.cutoff)));
   }
   SortParams p = sort_params(*ws, keys, tu);
   p.offsets = reinterpret_cast<const long long *>(offsets);
   p.num_roots = offsets ? num_arrays : 1;
   p.total = total;
+  p.readable[0] = total;
+  p.readable[1] = total + (long long)(kScratchPad / kb);
   KS_CUDA(ops(dt).seed(p, s));
-  KS_CUDA(ops(dt).sort(p, grid, s));
+  if (offsets || total > tu.cutoff) KS_CUDA(ops(dt).tiles(p, g.tiles, s));
+  KS_CUDA(ops(dt).smalls(p, g.smalls, s));
   return KSORT_OK;
 }
 
 // One warp waits for descriptor 0, which stays at generation 0 (never a live epoch).
-__global__ void selftest_wait_kernel(unsigned long long *lb, Control *ctl, unsigned *abort_flag,
+__global__ void selftest_wait_kernel(unsigned long long *lb, Control *ctl,
                                      unsigned long long limit_ns) {
   unsigned long long E = 0, steps = 0;
-  const int st = dev::lookback(lb, 1u, 0xffffffffu, limit_ns, abort_flag, &E, &steps);
-  if (threadIdx.x == 0 && st == 1) dev::raise_error(ctl, abort_flag, kDevTimeout, 0x400000000ull);
+  const int st = dev::lookback(lb, 1u, 0xffffffffu, limit_ns, &ctl->abort, &E, &steps);
+  if (threadIdx.x == 0 && st == 1) dev::raise_error(ctl, kDevTimeout, 0x400000000ull);
 }
 
 }  // namespace
@@ -374,8 +391,8 @@ ksort_status_t ksort_reserve_workspace(ksort_dtype_t dtype, int64_t max_total_ke
   Workspace *ws = nullptr;
   st = get_workspace(dev, (cudaStream_t)stream, need_for(dtype, max_total_keys, max_arrays), &ws);
   if (st != KSORT_OK) return st;
-  int grid = 0;  // also warms the occupancy cache (no queries during graph capture)
-  return full_grid(dtype, dev, g_tuning[dtype], &grid);
+  Grids g{};  // also warms the occupancy cache (no queries during graph capture)
+  return full_grids(dtype, dev, g_tuning[dtype], &g);
 }
 
 ksort_status_t ksort_release_workspace(ksort_stream_t stream) {
@@ -430,10 +447,6 @@ ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out) {
   out->smem_levels = c.smem_levels;
   out->lookback_steps = c.lookback_steps;
   out->items_pushed = c.pushed;  // pool slots: large and small items
-  out->cycles_fetch = c.cyc_fetch;
-  out->cycles_small = c.cyc_small;
-  out->cycles_tiles = c.cyc_tile;
-  out->cycles_finish = c.cyc_finish;
   return KSORT_OK;
 }
 
@@ -473,6 +486,14 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   return KSORT_OK;
 }
 
+ksort_status_t ksort_debug_trace(uint64_t *trace_dev, int64_t tickets) {
+  if (tickets < 0 || (tickets > 0 && !trace_dev)) return KSORT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_trace = reinterpret_cast<unsigned long long *>(trace_dev);
+  g_trace_cap = trace_dev ? tickets : 0;
+  return KSORT_OK;
+}
+
 ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stream) {
   if (limit_ms < 1 || limit_ms > 60000) return KSORT_ERR_INVALID_ARG;
   int dev = 0;
@@ -487,7 +508,7 @@ ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stre
   if ((st = get_workspace(dev, s, need, &ws)) != KSORT_OK) return st;
   KS_CUDA(cudaMemsetAsync(ws->lb, 0, sizeof(unsigned long long), s));
   KS_CUDA(cudaMemsetAsync(&ws->ctl->abort, 0, sizeof(unsigned), s));
-  selftest_wait_kernel<<<1, 32, 0, s>>>(ws->lb, ws->ctl, &ws->ctl->abort,
+  selftest_wait_kernel<<<1, 32, 0, s>>>(ws->lb, ws->ctl,
                                         (unsigned long long)limit_ms * 1000000ull);
   KS_CUDA(cudaGetLastError());
   return KSORT_OK;

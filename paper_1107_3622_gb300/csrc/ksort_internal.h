@@ -20,8 +20,9 @@ enum : unsigned {
 
 // Item flags.
 enum : unsigned {
-  kItemScratch = 1u,  // keys of the item live in the scratch buffer (else in the caller's)
-  kItemSmall = 2u,    // finished in shared memory by one CTA
+  kItemScratch = 1u,        // keys of the item live in buffer 1 (else in buffer 0)
+  kItemSmall = 2u,          // finished in shared memory by one CTA
+  kItemPartitionOnly = 4u,  // Steps 1-4 only: key and sides go to buffer 1, no recursion
 };
 
 // Largest sub-array, in keys, that one partition may handle: tile prefixes are
@@ -45,39 +46,24 @@ struct alignas(128) Control {
   // statistics of the last sort
   unsigned long long large_items, large_keys, tiles, small_items, small_keys;
   unsigned long long smem_levels, lookback_steps;
-  // SM cycles spent by the CTAs of the sort kernel, by phase (sum over CTAs)
-  unsigned long long cyc_fetch, cyc_small, cyc_tile, cyc_finish;
   unsigned long long pad1[3];
 };
 
 // One work item: a sub-array [begin, end) whose first element is its key.
-struct alignas(32) Item {
+struct alignas(16) Item {
   long long begin;
   long long end;
-  unsigned tiles;   // tile passes of a large item; 1 for a small item
-  unsigned lb;      // first look-back descriptor of a large item
-  unsigned flags;   // kItemScratch | kItemSmall
-  unsigned epoch;   // generation of the sort that wrote the item
+  unsigned long long key;  // bit pattern of the item's first element (its key, Step 1)
+  unsigned tiles;          // tile passes of a large item; 1 for a small item
+  unsigned lb;             // first tile ticket (= look-back descriptor) of a large item
+  unsigned flags;          // kItemScratch | kItemSmall | kItemPartitionOnly
+  unsigned epoch;          // generation of the sort that wrote the item
 };
 
 struct alignas(16) ItemCtl {
   unsigned grab;            // tiles handed out
   unsigned done;            // tiles finished
   unsigned long long less;  // #{x < key} of the item, written by its last tile
-};
-
-// State of the standalone partition, carried from call to call on one stream: tickets
-// and completions count up forever; `base` is their value when the current call
-// started and `gen` numbers the call (its look-back descriptors carry the generation).
-// The last CTA of a call advances `base` and `gen` and clears `abort`, so no memset is
-// needed between calls.
-struct alignas(64) PartCtl {
-  unsigned long long ticket;
-  unsigned long long done;
-  unsigned long long base;
-  unsigned long long less;
-  unsigned gen;
-  unsigned abort;
 };
 
 struct SortParams {
@@ -95,36 +81,30 @@ struct SortParams {
   long long num_roots;
   long long total;           // keys in buffer 0 that roots may cover
   int cutoff;                // largest small item
-  int pad;
+  unsigned root_flags;       // item flags of the roots (kItemPartitionOnly for a partition)
   unsigned long long spin_limit_ns;
+  long long *key_index;      // partition only: receives the key's index (device)
+  long long readable[2];     // elements [0, readable[j]) of buffer j may be read in bulk
+  unsigned long long *trace; // optional: kTraceWords timestamps per tile ticket
+  long long trace_cap;       // tickets the trace buffer holds
 };
-
-struct PartParams {
-  const void *in;
-  void *out;
-  long long n;
-  long long *key_index;
-  PartCtl *pctl;
-  unsigned long long *lb;
-  Control *ctl;  // receives device errors
-  unsigned long long spin_limit_ns;
-};
+constexpr int kTraceWords = 8;
 
 // Host-side launch interface, one explicit instantiation per key type.
 struct KernelInfo {
-  int block;          // threads per CTA
+  int block;          // threads per tile-pass CTA
   int tile_keys;      // keys per tile pass
-  int max_cutoff;     // largest shared-memory item the kernel supports
+  int max_cutoff;     // largest shared-memory item the kernels support
 };
 
 template <typename K>
 struct Launcher {
   static KernelInfo info();
-  static size_t sort_smem_bytes(int cutoff);
-  static cudaError_t max_ctas_per_sm(int cutoff, int *out);
-  static cudaError_t partition_out(const PartParams &p, int num_tiles, cudaStream_t s);
+  static size_t small_smem_bytes(int cutoff);
+  static cudaError_t occupancy(int cutoff, int *tile_ctas, int *small_ctas);
   static cudaError_t seed(const SortParams &p, cudaStream_t s);
-  static cudaError_t sort(const SortParams &p, int grid, cudaStream_t s);
+  static cudaError_t tiles(const SortParams &p, int grid, cudaStream_t s);
+  static cudaError_t smalls(const SortParams &p, int grid, cudaStream_t s);
   static long long tile_count(const void *buf, long long begin, long long end);
 };
 

@@ -6,76 +6,61 @@
 
 namespace ksort {
 
-// Compile-time shape of the kernels for a key type: threads per CTA, keys per thread
-// in a tile pass, the CTAs per SM the register budget is sized for, and the largest
-// shared-memory item.
+// Keys per thread of a tile pass: a tile is kTileThreads * IPT keys (8 KiB).
 template <typename K> struct Shape;
-template <> struct Shape<float> {
-  static constexpr int BLOCK = 256, IPT = 16, MINB = 4, MAX_CUTOFF = dev::kMaxSmallCutoff;
-};
-template <> struct Shape<unsigned> {
-  static constexpr int BLOCK = 256, IPT = 16, MINB = 4, MAX_CUTOFF = dev::kMaxSmallCutoff;
-};
-template <> struct Shape<double> {
-  static constexpr int BLOCK = 256, IPT = 8, MINB = 4, MAX_CUTOFF = 8192;
-};
+template <> struct Shape<float> { static constexpr int IPT = 16; };
+template <> struct Shape<unsigned> { static constexpr int IPT = 16; };
+template <> struct Shape<double> { static constexpr int IPT = 8; };
+
+template <typename K>
+constexpr int tile_keys() { return dev::kTileThreads * Shape<K>::IPT; }
 
 template <typename K>
 KernelInfo Launcher<K>::info() {
-  using S = Shape<K>;
-  return KernelInfo{S::BLOCK, S::BLOCK * S::IPT, S::MAX_CUTOFF};
+  return KernelInfo{dev::kTileThreads, tile_keys<K>(), dev::kMaxSmallCutoff};
 }
 
 template <typename K>
-size_t Launcher<K>::sort_smem_bytes(int cutoff) {
-  using S = Shape<K>;
-  const size_t stage = (size_t)2 * S::BLOCK * S::IPT * sizeof(K);
-  const size_t fin = dev::smem_finisher_bytes<K>(cutoff, S::BLOCK / 32);
-  return stage > fin ? stage : fin;
+size_t Launcher<K>::small_smem_bytes(int cutoff) {
+  return dev::small_smem_bytes<K>(cutoff);
 }
 
 template <typename K>
 long long Launcher<K>::tile_count(const void *buf, long long begin, long long end) {
-  using S = Shape<K>;
-  return dev::tile_count<K, S::BLOCK * S::IPT>(static_cast<const K *>(buf), begin, end);
+  return dev::tile_count<K, tile_keys<K>()>(static_cast<const K *>(buf), begin, end);
 }
 
 template <typename K>
-cudaError_t Launcher<K>::max_ctas_per_sm(int cutoff, int *out) {
-  using S = Shape<K>;
-  auto kern = dev::sort_kernel<K, S::BLOCK, S::IPT, S::MINB>;
-  const size_t smem = sort_smem_bytes(cutoff);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t Launcher<K>::occupancy(int cutoff, int *tile_ctas, int *small_ctas) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      tile_ctas, dev::tile_kernel<K, Shape<K>::IPT>, dev::kTileThreads, 0);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, S::BLOCK, smem);
-}
-
-template <typename K>
-cudaError_t Launcher<K>::partition_out(const PartParams &p, int num_tiles, cudaStream_t s) {
-  using S = Shape<K>;
-  auto kern = dev::partition_kernel<K, S::BLOCK, S::IPT>;
-  const size_t smem = (size_t)2 * S::BLOCK * S::IPT * sizeof(K);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto sk = dev::small_kernel<K>;
+  const size_t smem = small_smem_bytes(cutoff);
+  e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<num_tiles, S::BLOCK, smem, s>>>(p);
-  return cudaGetLastError();
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(small_ctas, sk, dev::kSmallThreads, smem);
 }
 
 template <typename K>
 cudaError_t Launcher<K>::seed(const SortParams &p, cudaStream_t s) {
-  using S = Shape<K>;
-  dev::seed_kernel<K, S::BLOCK * S::IPT><<<1, 1024, 0, s>>>(p);
+  dev::seed_kernel<K, tile_keys<K>()><<<1, 1024, 0, s>>>(p);
   return cudaGetLastError();
 }
 
 template <typename K>
-cudaError_t Launcher<K>::sort(const SortParams &p, int grid, cudaStream_t s) {
-  using S = Shape<K>;
-  auto kern = dev::sort_kernel<K, S::BLOCK, S::IPT, S::MINB>;
-  const size_t smem = sort_smem_bytes(p.cutoff);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t Launcher<K>::tiles(const SortParams &p, int grid, cudaStream_t s) {
+  dev::tile_kernel<K, Shape<K>::IPT><<<grid, dev::kTileThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t Launcher<K>::smalls(const SortParams &p, int grid, cudaStream_t s) {
+  auto sk = dev::small_kernel<K>;
+  const size_t smem = small_smem_bytes(p.cutoff);
+  cudaError_t e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, S::BLOCK, smem, s>>>(p);
+  sk<<<grid, dev::kSmallThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
