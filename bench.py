@@ -351,7 +351,7 @@ def run_ours(args, dist: Dist):
                    "vs_baseline_ref": "Table 1 K-sort 3.2892 s at n=7e6 (paper's CPU)"},
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,  # seed_kernel + tile_kernel + small_kernel per sort
         "clocks": clocks.summary(),
         "timed_wall_s": round(wall, 3),
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),
