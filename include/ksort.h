@@ -57,7 +57,9 @@ typedef enum {
                                          or one array exceeds 2^31 - 1 keys           */
     KSORT_ERR_WORKSPACE_EXHAUSTED = 7,/* device: the work queue or look-back arena was
                                          too small (adversarial, near-O(n^2) inputs)   */
-    KSORT_ERR_INTERNAL = 8
+    KSORT_ERR_INTERNAL = 8,
+    KSORT_ERR_TOO_LARGE = 9           /* n above KSORT_NOALLOC_MAX_KEYS (the fixed
+                                         scratch of ksort_partition_out_noalloc)      */
 } ksort_status_t;
 
 /* Steps 1-4 once, in place, on keys_dev[0..n-1] (Section 1.1, Steps 1-4).
@@ -72,6 +74,39 @@ KSORT_API ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, in
  * in_dev) receives the partitioned keys. One read and one write pass over the keys. */
 KSORT_API ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
                                    int64_t n, int64_t *key_index_dev, ksort_stream_t stream);
+
+/* ksort_partition_out without any allocation. The paper has no counterpart: it is a
+ * library form for callers that must not allocate device memory. Examples are a
+ * process that has given all free HBM to its own pool allocator (cudaMalloc would
+ * fail there), and a latency-bound caller that shares the GPU (cudaFree synchronises
+ * the whole device, which would stall every other stream). Every other entry point
+ * allocates a per-stream workspace on first use, of at least 2^21 look-back
+ * descriptors (tens of MB).
+ *
+ * Arguments, result and checks are those of ksort_partition_out, for
+ * 1 <= n <= KSORT_NOALLOC_MAX_KEYS. A larger n returns KSORT_ERR_TOO_LARGE and enqueues
+ * nothing. The call allocates nothing: the scratch of the partition kernels (control
+ * block, work item, look-back descriptors, ticket map: about 67 KB) is one
+ * file-scope device array, one copy per device, and out_dev takes the keys directly.
+ *
+ * The first call on a device does set-up with that device current: it looks up the
+ * array's device address (cudaGetSymbolAddress), reads the SM count and the kernel
+ * occupancy, and clears the array on `stream`. Make that first call before any stream
+ * capture.
+ *
+ * Every call on a device shares the one array, which keeps the last call's contents.
+ * Each call clears the words that must start at zero (the sticky error word). A new
+ * generation number retires the rest. Calls that overlap on the GPU race on the array
+ * and give wrong results: different streams without an ordering event, or several host
+ * threads. Order them, e.g. on one stream.
+ *
+ * Errors found on the device (a look-back wait past the tuned time limit, an
+ * inconsistent descriptor) are not recorded for ksort_get_device_error(). Instead
+ * *key_index_dev receives the negated status (for example -KSORT_ERR_TIMEOUT). */
+#define KSORT_NOALLOC_MAX_KEYS (1LL << 24)
+KSORT_API ksort_status_t ksort_partition_out_noalloc(ksort_dtype_t dtype, const void *in_dev,
+                                           void *out_dev, int64_t n, int64_t *key_index_dev,
+                                           ksort_stream_t stream);
 
 /* Steps 1-6: sorts keys_dev[0..n-1] ascending, in place (Section 1.1). The recursion of
  * Steps 5-6 runs on the device (persistent kernel with a work queue); sub-arrays of at

@@ -18,7 +18,7 @@ import threading
 
 __all__ = [
     "KSortError", "F32", "F64", "U32", "load", "library_path",
-    "ksort_partition", "ksort_partition_out", "ksort_sort", "ksort_sort_batched",
+    "ksort_partition", "ksort_partition_out", "ksort_partition_out_noalloc", "ksort_sort", "ksort_sort_batched",
     "ksort_reserve_workspace", "ksort_release_workspace", "ksort_get_device_error",
     "ksort_get_stats", "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
     "ksort_tile_keys", "ksort_status_string", "ksort_last_cuda_error",
@@ -27,6 +27,8 @@ __all__ = [
 ]
 
 F32, F64, U32 = 0, 1, 2
+KSORT_ERR_TOO_LARGE = 9
+KSORT_NOALLOC_MAX_KEYS = 1 << 24
 _NAMES = {F32: "f32", F64: "f64", U32: "u32"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -84,6 +86,7 @@ def load():
         sig = {
             "ksort_partition": (i32, [i32, vp, i64, vp, vp]),
             "ksort_partition_out": (i32, [i32, vp, vp, i64, vp, vp]),
+            "ksort_partition_out_noalloc": (i32, [i32, vp, vp, i64, vp, vp]),
             "ksort_sort": (i32, [i32, vp, i64, vp]),
             "ksort_sort_batched": (i32, [i32, vp, vp, i64, i64, vp]),
             "ksort_reserve_workspace": (i32, [i32, i64, i64, vp]),
@@ -163,6 +166,13 @@ def ksort_partition(dtype: int, keys, n: int, key_index, stream=None):
 def ksort_partition_out(dtype: int, src, dst, n: int, key_index, stream=None):
     _check(load().ksort_partition_out(dtype, _ptr(src), _ptr(dst), n, _ptr(key_index),
                                       _stream(stream)), "ksort_partition_out")
+
+
+def ksort_partition_out_noalloc(dtype: int, src, dst, n: int, key_index, stream=None):
+    """Same as ksort_partition_out, with the kernels' scratch in a fixed device array
+    (n <= KSORT_NOALLOC_MAX_KEYS). A device-side error shows as a negative key index."""
+    _check(load().ksort_partition_out_noalloc(dtype, _ptr(src), _ptr(dst), n, _ptr(key_index),
+                                              _stream(stream)), "ksort_partition_out_noalloc")
 
 
 def ksort_sort(dtype: int, keys, n: int, stream=None):

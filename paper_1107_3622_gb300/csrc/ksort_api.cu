@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -353,6 +354,125 @@ __global__ void selftest_wait_kernel(unsigned long long *lb, Control *ctl,
   if (threadIdx.x == 0 && st == 1) dev::raise_error(ctl, kDevTimeout, 0x400000000ull);
 }
 
+// ------------------------------------------------------------------ fixed-scratch partition
+// ksort_partition_out_noalloc runs the same seed and tile kernels as
+// ksort_partition_out, but keeps their control block, work item, look-back descriptors
+// and ticket map in one file-scope device array instead of a per-stream workspace, so
+// that a call allocates nothing. Layout: [Control][items][item counters][small list]
+// [look-back][ticket map].
+constexpr unsigned long long kNoallocItems = 4;  // a single partition queues only its root
+// Tile tickets of the largest input: KSORT_NOALLOC_MAX_KEYS keys at the smallest tile
+// (4096 float64 keys), plus one for a start that is not tile-aligned, plus slack.
+constexpr unsigned long long kNoallocTiles = KSORT_NOALLOC_MAX_KEYS / 4096 + 64;
+constexpr size_t kNoallocItemsOff = (sizeof(Control) + 255) / 256 * 256;
+constexpr size_t kNoallocIctlOff = kNoallocItemsOff + kNoallocItems * sizeof(Item);
+constexpr size_t kNoallocSqOff = kNoallocIctlOff + kNoallocItems * sizeof(ItemCtl);
+constexpr size_t kNoallocLbOff = (kNoallocSqOff + kNoallocItems * 8 + 255) / 256 * 256;
+constexpr size_t kNoallocTmapOff = kNoallocLbOff + kNoallocTiles * 8;
+constexpr size_t kNoallocBytes = kNoallocTmapOff + kNoallocTiles * 8;  // about 67 KB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+struct NoallocDevice {
+  bool ready = false;
+  unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
+  int sms = 0;
+  int tile_ctas[3] = {0, 0, 0};   // tile_kernel CTAs per SM, per dtype
+};
+NoallocDevice g_noalloc[kNoallocMaxDevices];
+
+// First call on a device (with that device current): look up the array's address,
+// read the SM count and the tile kernel's occupancy, and clear the array on `s`.
+ksort_status_t noalloc_device(int dev, cudaStream_t s, NoallocDevice **out) {
+  if (dev < 0 || dev >= kNoallocMaxDevices) return KSORT_ERR_INVALID_ARG;
+  NoallocDevice &d = g_noalloc[dev];
+  if (!d.ready) {
+    void *base = nullptr;
+    KS_CUDA(cudaGetSymbolAddress(&base, g_noalloc_scratch));
+    KS_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int t = 0; t < 3; ++t) {
+      int small_ctas = 0;
+      KS_CUDA(ops((ksort_dtype_t)t).occupancy(g_tuning[t].cutoff, &d.tile_ctas[t], &small_ctas));
+      if (d.tile_ctas[t] < 1) return KSORT_ERR_INTERNAL;
+    }
+    KS_CUDA(cudaMemsetAsync(base, 0, kNoallocBytes, s));
+    d.base = static_cast<unsigned char *>(base);
+    d.ready = true;
+  }
+  *out = &d;
+  return KSORT_OK;
+}
+
+// Runs after the tile pass: a device-side error becomes a negative key index, and the
+// next call starts with a clear flag.
+__global__ void noalloc_status_kernel(Control *ctl, long long *key_index) {
+  const unsigned e = ctl->error;
+  if (e) *key_index = -(long long)e;
+}
+
+ksort_status_t partition_noalloc_impl(ksort_dtype_t dt, const void *in, void *out, int64_t n,
+                                      int64_t *key_index, cudaStream_t s) {
+  if (!dtype_ok(dt)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (n < 1) return KSORT_ERR_INVALID_ARG;
+  if (n > KSORT_NOALLOC_MAX_KEYS) return KSORT_ERR_TOO_LARGE;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  const size_t kb = key_bytes(dt);
+  if ((st = check_device_ptr(in, kb, dev)) != KSORT_OK) return st;
+  if ((st = check_device_ptr(out, kb, dev)) != KSORT_OK) return st;
+  if ((st = check_device_ptr(key_index, 8, dev)) != KSORT_OK) return st;
+  {
+    const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+    if (a < b + n * kb && b < a + n * kb) return KSORT_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  NoallocDevice *d = nullptr;
+  if ((st = noalloc_device(dev, s, &d)) != KSORT_OK) return st;
+  if (n == 1) {
+    KS_CUDA(cudaMemsetAsync(key_index, 0, sizeof(int64_t), s));
+    KS_CUDA(cudaMemcpyAsync(out, in, kb, cudaMemcpyDeviceToDevice, s));
+    return KSORT_OK;
+  }
+  const long long tiles = ops(dt).tile_count(in, 0, n);
+  if ((unsigned long long)tiles > kNoallocTiles) return KSORT_ERR_TOO_LARGE;
+  const Tuning tu = g_tuning[dt];
+  unsigned char *b = d->base;
+  Control *ctl = reinterpret_cast<Control *>(b);
+  SortParams p{};
+  p.keys = const_cast<void *>(in);
+  p.scratch = out;
+  p.ctl = ctl;
+  p.items = reinterpret_cast<Item *>(b + kNoallocItemsOff);
+  p.ictl = reinterpret_cast<ItemCtl *>(b + kNoallocIctlOff);
+  p.small_q = reinterpret_cast<unsigned long long *>(b + kNoallocSqOff);
+  p.item_cap = kNoallocItems;
+  p.lb = reinterpret_cast<unsigned long long *>(b + kNoallocLbOff);
+  p.tmap = reinterpret_cast<unsigned long long *>(b + kNoallocTmapOff);
+  p.lb_cap = kNoallocTiles;
+  p.num_roots = 1;
+  p.total = n;
+  p.cutoff = tu.cutoff;
+  p.root_flags = kItemPartitionOnly;
+  p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
+  p.key_index = reinterpret_cast<long long *>(key_index);
+  p.readable[0] = n;
+  p.readable[1] = 0;  // the output is only written
+  // The seed kernel resets every dispatch counter and moves to a new generation, which
+  // retires the descriptors and ticket-map entries of earlier calls; only the sticky
+  // error word and its info must be cleared here.
+  const size_t e0 = offsetof(Control, error), e1 = offsetof(Control, err_info) + 8;
+  KS_CUDA(cudaMemsetAsync(b + e0, 0, e1 - e0, s));
+  const int grid = (int)std::max<long long>(
+      1, std::min<long long>((long long)d->sms * d->tile_ctas[dt], tiles));
+  KS_CUDA(ops(dt).seed(p, s));
+  KS_CUDA(ops(dt).tiles(p, grid, s));
+  noalloc_status_kernel<<<1, 1, 0, s>>>(ctl, p.key_index);
+  KS_CUDA(cudaGetLastError());
+  return KSORT_OK;
+}
+
 }  // namespace
 }  // namespace ksort
 
@@ -368,6 +488,12 @@ ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, int64_t n,
 ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
                                    int64_t n, int64_t *key_index_dev, ksort_stream_t stream) {
   return partition_impl(dtype, in_dev, out_dev, n, key_index_dev, (cudaStream_t)stream, false);
+}
+
+ksort_status_t ksort_partition_out_noalloc(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
+                                           int64_t n, int64_t *key_index_dev,
+                                           ksort_stream_t stream) {
+  return partition_noalloc_impl(dtype, in_dev, out_dev, n, key_index_dev, (cudaStream_t)stream);
 }
 
 ksort_status_t ksort_sort(ksort_dtype_t dtype, void *keys_dev, int64_t n, ksort_stream_t stream) {
@@ -525,6 +651,7 @@ const char *ksort_status_string(ksort_status_t s) {
     case KSORT_ERR_BAD_OFFSETS: return "bad offsets";
     case KSORT_ERR_WORKSPACE_EXHAUSTED: return "work queue or look-back arena exhausted";
     case KSORT_ERR_INTERNAL: return "internal error";
+    case KSORT_ERR_TOO_LARGE: return "n exceeds the fixed scratch of ksort_partition_out_noalloc (KSORT_NOALLOC_MAX_KEYS = 2^24 keys)";
   }
   return "unknown status";
 }

@@ -44,7 +44,7 @@ def test_library_is_in_tree(lib):
 
 def test_status_strings(lib):
     import paper_1107_3622_gb300 as ks
-    for code in range(9):
+    for code in range(10):
         assert ks.ksort_status_string(code) and "unknown" not in ks.ksort_status_string(code)
     assert "unknown" in ks.ksort_status_string(99)
 
@@ -58,6 +58,8 @@ def test_host_side_rejections_need_no_gpu(lib):
     assert lib.ksort_partition(0, None, 0, None, None) == 1         # n == 0
     assert lib.ksort_partition(5, None, 4, None, None) == 2
     assert lib.ksort_selftest_wait_timeout(0, None) == 1
+    assert lib.ksort_partition_out_noalloc(0, None, None, (1 << 24) + 1, None, None) == 9
+    assert lib.ksort_partition_out_noalloc(0, None, None, 0, None, None) == 1
 
 
 def test_tuning_validation(lib):

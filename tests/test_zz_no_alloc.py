@@ -1,0 +1,130 @@
+"""ksort_partition_out_noalloc: the partition of Steps 1-4 (Section 1.1) with the kernels'
+scratch in one fixed device array, so that a call allocates nothing. Its results must
+equal those of ksort_partition_out (the same kernels on a per-stream workspace) and the
+oracle's key index, on two calls in a row that share the array.
+
+This file is collected last on purpose. It must pass in a fresh process, where its first
+call does the per-device set-up, and after every other test has used the library."""
+import numpy as np
+import pytest
+
+import ksort_inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = ["f32", "f64", "u32"]
+
+
+@pytest.fixture(scope="module")
+def ks():
+    import torch
+    import paper_1107_3622_gb300 as ks
+    ks.load()
+    torch.cuda.set_device(0)
+    return ks
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _poisoned(like):
+    import torch
+    t = torch.empty_like(like)
+    t.view(torch.uint8).fill_(0xAB)
+    return t
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+def _oracle_index(ref, a):
+    b = a.copy()
+    i, *_ = ref.partition(b)
+    return i
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_two_calls_in_a_row_match_partition_out(ref, ks, dtype):
+    """Two back-to-back calls on one stream (the second smaller than the first, with a
+    misaligned start), then the same two inputs through ksort_partition_out."""
+    import torch
+    code = {"f32": ks.F32, "f64": ks.F64, "u32": ks.U32}[dtype]
+    a1 = gen.make("uniform", dtype, 1_000_003, gen.seed_for(5, 1, 0))
+    big = gen.make("uniform", dtype, 70_002, gen.seed_for(5, 2, 0))
+    a2 = big[1:]
+    s1 = _dev(a1)
+    s2 = _dev(big)[1:]
+    g1, g2 = _poisoned(s1), _poisoned(s2)
+    w1, w2 = _poisoned(s1), _poisoned(s2)
+    idx = torch.full((4,), -99, dtype=torch.int64, device="cuda")
+    ks.ksort_partition_out_noalloc(code, s1, g1, a1.size, idx[0:1])
+    ks.ksort_partition_out_noalloc(code, s2, g2, a2.size, idx[1:2])
+    ks.ksort_partition_out(code, s1, w1, a1.size, idx[2:3])
+    ks.ksort_partition_out(code, s2, w2, a2.size, idx[3:4])
+    torch.cuda.synchronize()
+    assert ks.ksort_get_device_error() == 0
+    i1, i2, j1, j2 = idx.tolist()
+    assert (i1, i2) == (j1, j2)
+    assert i1 == _oracle_index(ref, a1) and i2 == _oracle_index(ref, a2)
+    assert _host(g1).tobytes() == _host(w1).tobytes()
+    assert _host(g2).tobytes() == _host(w2).tobytes()
+    assert _host(s1).tobytes() == a1.tobytes()  # inputs untouched
+    assert _host(s2).tobytes() == a2.tobytes()
+
+
+def test_largest_size_and_one_key(ref, ks):
+    """n = KSORT_NOALLOC_MAX_KEYS float64 keys from a start that is not tile-aligned
+    (the most tile tickets the fixed array must hold), then n = 1."""
+    import torch
+    n = ks.KSORT_NOALLOC_MAX_KEYS
+    big = gen.make("uniform", "f64", n + 1, gen.seed_for(5, 3, 0))
+    src = _dev(big)[1:]
+    got, want = _poisoned(src), _poisoned(src)
+    idx = torch.full((2,), -99, dtype=torch.int64, device="cuda")
+    ks.ksort_partition_out_noalloc(ks.F64, src, got, n, idx[0:1])
+    ks.ksort_partition_out(ks.F64, src, want, n, idx[1:2])
+    torch.cuda.synchronize()
+    i, j = idx.tolist()
+    assert i == j == _oracle_index(ref, big[1:])
+    assert torch.equal(got.view(torch.int64), want.view(torch.int64))
+    one_in = _dev(np.array([0.25], np.float64))
+    one_out = _poisoned(one_in)
+    ks.ksort_partition_out_noalloc(ks.F64, one_in, one_out, 1, idx[0:1])
+    torch.cuda.synchronize()
+    assert int(idx[0].item()) == 0 and float(one_out.item()) == 0.25
+
+
+def test_rejects_beyond_the_maximum_and_enqueues_nothing(ks):
+    import torch
+    n = ks.KSORT_NOALLOC_MAX_KEYS + 1
+    src = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dst = _poisoned(src)
+    idx = torch.full((1,), -99, dtype=torch.int64, device="cuda")
+    with pytest.raises(ks.KSortError) as e:
+        ks.ksort_partition_out_noalloc(ks.F32, src, dst, n, idx)
+    assert e.value.status == ks.KSORT_ERR_TOO_LARGE
+    assert "KSORT_NOALLOC_MAX_KEYS" in str(e.value)
+    torch.cuda.synchronize()
+    assert int(idx.item()) == -99
+    assert bool((dst.view(torch.uint8) == 0xAB).all())
+
+
+def test_calls_leave_free_device_memory_unchanged(ks):
+    """After the set-up call, further calls take no device memory."""
+    import torch
+    a = gen.make("uniform", "f32", 300_000, gen.seed_for(5, 4, 0))
+    src = _dev(a)
+    dst = torch.empty_like(src)
+    idx = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ks.ksort_partition_out_noalloc(ks.F32, src, dst, a.size, idx)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        ks.ksort_partition_out_noalloc(ks.F32, src, dst, a.size, idx)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert int(idx.item()) == int((torch.from_numpy(a[1:]) < float(a[0])).sum())
