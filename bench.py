@@ -13,6 +13,10 @@ Also reported on the same line:
   partition_pass ksort_partition_out alone at the same size (buffers rotated > L2)
   batched        4096 log-uniform arrays: one graph-replayed ksort_sort_batched vs a
                  loop of per-array ksort_sort launches
+  serving        10,000 Poisson requests (log-uniform 1e3..1e7 keys, half float32, half
+                 uint32) served by continuous batching on a stream pool at 0.8 x the
+                 measured batched capacity: keys/s, p50/p99 latency, and every result
+                 checked equal to the same request sorted alone
   clocks         SM clock and throttle reasons sampled during the timed region
 
 --impl reference times the oracle itself (the CPU program written from the paper) as
@@ -46,6 +50,10 @@ METRIC = "keys/sec at n=7e6 fp32 U[0,1]; batched vs per-array launch; % of HBM r
 UNIT = "keys/s"
 PAPER_KSORT_S_AT_7E6 = 3.2892  # Table 1, K-sort mean time at n = 7,000,000
 PAPER_KEYS_PER_S = N_KEYS / PAPER_KSORT_S_AT_7E6
+# Table 1: K-sort mean time (s) per n on the paper's machine (key type not stated)
+PAPER_TABLE1_S = {100_000: 0.0157, 500_000: 0.0811, 1_000_000: 0.1877, 2_500_000: 0.6532,
+                  5_000_000: 1.914, 6_000_000: 2.5967, 7_000_000: 3.2892, 7_100_000: 3.4502,
+                  7_500_000: 4.0695, 10_000_000: 8.2293}
 L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = "ksort_sort n=7e6 float32 U[0,1] (Table 1 size)"
 DEVICE_SOURCES = ("paper_1107_3622_gb300/csrc/ksort_device.cuh",
@@ -61,7 +69,18 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=N_KEYS)
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip partition_pass, batched and cpu_baseline")
+                    help="skip every extra (partition_pass, batched, serving, cpu_baseline)")
+    ap.add_argument("--extras", default="partition,batched,serving,cpu",
+                    help="comma-separated extras to run: partition, batched, serving, cpu")
+    ap.add_argument("--sweep", action="store_true",
+                    help="instead of the headline line: the Table 1 size sweep (float32 and "
+                         "float64, 20 repetitions per size) as one JSON line")
+    ap.add_argument("--sweep-oracle-reps", type=int, default=2,
+                    help="oracle repetitions per size in --sweep (0 skips the oracle)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the library's default tuning instead of the autotuned one")
+    ap.add_argument("--serving-requests", type=int, default=10_000,
+                    help="requests of the serving run (0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="time budget of the cpu_baseline sample")
     return ap.parse_args(argv)
@@ -262,6 +281,20 @@ def cpu_baseline(n: int, budget_s: float, seed: int):
 
 
 # ----------------------------------------------------------------------------- ours
+def autotune_sort(ks, n: int, args) -> dict:
+    """Tile shape, cutoff and finisher CTAs for the timed workload: the project's
+    autotuner (searched in this process, on this GPU), or the defaults."""
+    from paper_1107_3622_gb300 import autotune
+    if args.no_autotune:
+        autotune.reset(ks.F32)
+        return dict(ks.ksort_get_tuning(ks.F32), autotuned=False)
+    e = autotune.autotune("sort", ks.F32, n=n, reps=3)
+    shape = ks.ksort_tile_shape(ks.F32, e["tuning"]["tile_shape"])
+    return dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
+                keys_per_thread=shape[1], staged=shape[2], search_ms=e["ms"],
+                candidates=len(e.get("candidates", [])), cached=e["cached"])
+
+
 def run_ours(args, dist: Dist):
     import torch
 
@@ -277,6 +310,7 @@ def run_ours(args, dist: Dist):
     pristine = torch.from_numpy(host).to(dev)
     keys = torch.empty_like(pristine)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    tuning = autotune_sort(ks, n, args)
     ks.ksort_reserve_workspace(ks.F32, n, 1)
 
     def prep():
@@ -348,7 +382,8 @@ def run_ours(args, dist: Dist):
                    "parallelism": f"replicas x{dist.world} (independent arrays)",
                    "l2": "flushed before every step (256 MiB write), input restored by an "
                          "untimed device copy; per-step CUDA events around ksort_sort",
-                   "vs_baseline_ref": "Table 1 K-sort 3.2892 s at n=7e6 (paper's CPU)"},
+                   "vs_baseline_ref": "Table 1 K-sort 3.2892 s at n=7e6 (paper's CPU)",
+                   "tuning": tuning},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": 3 * args.steps,  # seed_kernel + tile_kernel + small_kernel per sort
@@ -358,13 +393,20 @@ def run_ours(args, dist: Dist):
                     "max": round(max(step_ms), 4)},
         "sort_stats": stats,
     }
-    if dist.rank == 0 and not args.no_extras:
-        line["partition_pass"] = run_partition_pass(ks, n, peak, peak_src)
-        line["batched"] = run_batched(ks)
-        v, sample, spent = cpu_baseline(min(n, N_KEYS), args.cpu_seconds, None)
-        line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample, "seconds": round(spent, 2),
-                                "host_cpus": os.cpu_count()}
+    extras = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
+    if dist.rank == 0:
+        if "partition" in extras:
+            line["partition_pass"] = run_partition_pass(ks, n, peak, peak_src)
+        if "batched" in extras:
+            line["batched"] = run_batched(ks, args)
+        if "serving" in extras and args.serving_requests > 0:
+            bt = line.get("batched", {}).get("batched_tuning") or ks.ksort_get_tuning(ks.F32)
+            line["serving"] = run_serving(ks, args.serving_requests, bt)
+        if "cpu" in extras:
+            v, sample, spent = cpu_baseline(min(n, N_KEYS), args.cpu_seconds, None)
+            line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1,
+                                    "kind": "oracle", "sample": sample,
+                                    "seconds": round(spent, 2), "host_cpus": os.cpu_count()}
     return line
 
 
@@ -433,11 +475,22 @@ def run_partition_pass(ks, n, peak, peak_src):
                       "CUDA events around back-to-back launches"}
 
 
-def run_batched(ks):
+def run_batched(ks, args):
     """4096 arrays, lengths log-uniform in [100, 1e6]: one CUDA-graph replay of
-    ksort_sort_batched vs a loop of per-array ksort_sort launches (same stream)."""
+    ksort_sort_batched (autotuned) vs a loop of per-array ksort_sort launches (same
+    stream, the timed workload's tuning)."""
     import torch
+    from paper_1107_3622_gb300 import autotune
+    sort_tuning = ks.ksort_get_tuning(ks.F32)
     lengths = gen.batched_lengths()
+    if args.no_autotune:
+        autotune.reset(ks.F32)
+        tuned = {"autotuned": False}
+    else:
+        e = autotune.autotune("batched", ks.F32, lengths=lengths, reps=2)
+        tuned = {"autotuned": True, "search_ms": e["ms"], "cached": e["cached"],
+                 "candidates": len(e.get("candidates", []))}
+    batched_tuning = dict(ks.ksort_get_tuning(ks.F32), **tuned)
     off = gen.offsets_from_lengths(lengths)
     total = int(off[-1])
     pristine = gen.uniform_torch("f32", gen.seed_for(2, 0, 0), total, device="cuda")
@@ -468,7 +521,10 @@ def run_batched(ks):
     batched_out = keys.clone()
     t_batched = min(times)
 
-    # per-array loop
+    # per-array loop, under the single-array tuning
+    ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
+                        ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
+                        tile_shape=sort_tuning["tile_shape"])
     bounds = [(int(off[r]), int(off[r + 1])) for r in range(len(lengths))]
     keys.copy_(pristine)
     for b, e in bounds[:16]:
@@ -490,7 +546,113 @@ def run_batched(ks):
             "graph_batched_keys_per_s": round(total / (t_batched / 1e3), 1),
             "per_array_loop_ms": round(t_loop, 3),
             "per_array_loop_keys_per_s": round(total / (t_loop / 1e3), 1),
-            "speedup": round(t_loop / t_batched, 2), "outputs_identical": same}
+            "speedup": round(t_loop / t_batched, 2), "outputs_identical": same,
+            "batched_tuning": batched_tuning, "loop_tuning": sort_tuning}
+
+
+def run_serving(ks, count: int, tuning: dict):
+    """Serving configuration: `count` Poisson requests, sizes log-uniform in
+    [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys resident in HBM; the rate is
+    0.8 x the batched capacity measured on the same size mix, / mean keys per request."""
+    import torch
+    from paper_1107_3622_gb300 import serving
+    # serving batches take the batched form's tuning, for both 4-byte key types
+    for code in (ks.F32, ks.U32):
+        ks.ksort_set_tuning(code, cutoff=tuning["cutoff"], ctas_per_sm=tuning["ctas_per_sm"] or -1,
+                            tile_shape=tuning["tile_shape"])
+    cap = serving.measure_capacity()
+    rate = 0.8 * cap / serving.mean_length()
+    reqs = serving.poisson_requests(count, rate)
+    t0 = time.perf_counter()
+    pools = serving.build_pools(reqs)
+    gen_s = time.perf_counter() - t0
+    srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
+    res = srv.run(reqs, pools)
+    out = res.summary()
+    # every result against the same request sorted alone
+    t0 = time.perf_counter()
+    mismatches = 0
+    for r in reqs:
+        got = pools[r.dtype][r.pool_off:r.pool_off + r.n]
+        alone = serving.sort_alone(r)
+        if not torch.equal(got.view(torch.int32), alone.view(torch.int32)):
+            mismatches += 1
+        del alone
+    if ks.ksort_get_device_error():
+        raise RuntimeError("device error in the serving check")
+    out.update({"rate_per_s": round(rate, 1), "capacity_keys_per_s": round(cap, 1),
+                "slots": len(srv.slots), "slot_keys": 1 << 27,
+                "alone_vs_mix_identical": mismatches == 0, "checked": len(reqs),
+                "mismatches": mismatches, "check_s": round(time.perf_counter() - t0, 2),
+                "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning[k] for k in
+                                                           ("cutoff", "ctas_per_sm", "tile_shape")},
+                "latency": "arrival -> completion event of the request's batch"})
+    del pools
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_sweep(args):
+    """Table 1 sizes, float32 and float64 U[0,1], 20 seeded repetitions each (rep r =
+    seed rep r): mean ksort_sort time (CUDA events, L2 flushed and input restored before
+    every run), keys/s, algorithmic GB/s of the sort and its fraction of the measured HBM
+    peak, every output checked sorted; the oracle's mean time on a few of the same arrays."""
+    import torch
+    import paper_1107_3622_gb300 as ks
+    import oracle
+    torch.cuda.set_device(0)
+    ks.load()
+    oracle.build()
+    peak, peak_src = measured_peaks()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    reps = 20
+    rows = []
+    for name, code, kb in (("f32", ks.F32, 4), ("f64", ks.F64, 8)):
+        ks.ksort_reserve_workspace(code, max(gen.TABLE1_SIZES), 1)
+        for si, n in enumerate(gen.TABLE1_SIZES):
+            cfg = 1 if name == "f32" else 2
+            ms, algo = [], []
+            for r in range(reps):
+                keys = gen.uniform_torch(name, gen.seed_for(cfg, si, r), n, device="cuda")
+                if r == 0:  # warm-up on the first array
+                    w = keys.clone()
+                    ks.ksort_sort(code, w, n)
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ks.ksort_sort(code, keys, n)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                st = ks.ksort_get_stats()
+                algo.append(2 * kb * (st["large_keys"] + st["small_keys"]))
+                if not bool((keys[1:] >= keys[:-1]).all()):
+                    raise RuntimeError(f"unsorted output at n={n} {name} rep {r}")
+            if ks.ksort_get_device_error():
+                raise RuntimeError("device error in the sweep")
+            mean_ms = statistics.fmean(ms)
+            gbs = statistics.fmean(algo) / (mean_ms / 1e3) / 1e9
+            row = {"dtype": name, "n": n, "reps": reps, "mean_ms": round(mean_ms, 4),
+                   "min_ms": round(min(ms), 4), "keys_per_s": round(n / (mean_ms / 1e3), 1),
+                   "algorithmic_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                   "lower_bound_frac": round(2 * kb * n / (mean_ms / 1e3) / 1e9 / peak, 5),
+                   "paper_table1_s": PAPER_TABLE1_S[n]}
+            if args.sweep_oracle_reps > 0:
+                t = []
+                for r in range(args.sweep_oracle_reps):
+                    a = gen.make("uniform", name, n, gen.seed_for(cfg, si, r))
+                    t0 = time.perf_counter()
+                    oracle.sort(a)
+                    t.append(time.perf_counter() - t0)
+                row["oracle_mean_s"] = round(statistics.fmean(t), 4)
+                row["oracle_reps"] = len(t)
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    return {"sweep": "Table 1 sizes, ksort_sort, f32 and f64 U[0,1]", "peak": peak,
+            "peak_source": f"{peak_src} hbm_gbs", "tuning": {"f32": ks.ksort_get_tuning(ks.F32),
+                                                             "f64": ks.ksort_get_tuning(ks.F64)},
+            "oracle": "C oracle, 1 thread, gcc -O2", "rows": rows}
 
 
 # ----------------------------------------------------------------------------- reference
@@ -547,6 +709,9 @@ def main(argv=None):
             return 0
         line = run_reference(args, _NoDist())
         print(json.dumps(line), flush=True)
+        return 0
+    if args.sweep:
+        print(json.dumps(run_sweep(args)), flush=True)
         return 0
     dist = Dist(args.gpus)
     try:

@@ -149,23 +149,38 @@ typedef struct {
 } ksort_stats_t;
 KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out);
 
-/* Tuning for one dtype (process-wide). Zero fields keep their current value.
+/* Tuning for one dtype (process-wide; the autotuner sets it). Zero fields keep their
+ * current value.
  *   cutoff:        sub-arrays with at most this many keys are finished in shared
  *                  memory (2 .. ksort_max_cutoff(dtype));
- *   ctas_per_sm:   persistent-kernel CTAs per SM (capped by occupancy);
- *   spin_limit_ms: time limit of every device-side wait. */
+ *   ctas_per_sm:   shared-memory finisher CTAs per SM (capped by occupancy);
+ *                  -1 = as many as fit (the default);
+ *   spin_limit_ms: time limit of every device-side wait (1 .. 600000);
+ *   tile_shape:    form of the partition passes, 1 .. 6 (1 = default); see
+ *                  ksort_tile_shape(). Changing it may grow a stream's workspace on
+ *                  the next call, so reserve again before capturing a graph.
+ * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
     int32_t ctas_per_sm;
     int32_t spin_limit_ms;
-    int32_t reserved;
+    int32_t tile_shape;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);
 KSORT_API int32_t ksort_max_cutoff(ksort_dtype_t dtype);
 
-/* Keys handled by one tile pass of the partition kernels for `dtype`. */
+/* Keys handled by one tile pass of the partition kernels for `dtype` under the current
+ * tuning (threads x keys per thread of its tile shape). */
 KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
+
+/* Form `shape` (1 .. 6) of the partition passes for `dtype`: *threads CTA threads, each
+ * holding *keys_per_thread keys (a multiple of the 128-bit vector). Forms 1-3 load a
+ * tile straight into registers. Forms 4-6 (*staged = 1) have the same shapes as 1-3,
+ * but stage the next tile into shared memory by a bulk copy while the current one is
+ * finished. */
+KSORT_API ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
+                                          int32_t *keys_per_thread, int32_t *staged);
 
 /* Failure-path check: runs one device-side wait, of the kind the partition's look-back
  * uses, on a flag that nothing ever sets. The wait gives up after limit_ms (1..60000),

@@ -21,7 +21,7 @@ __all__ = [
     "ksort_partition", "ksort_partition_out", "ksort_partition_out_noalloc", "ksort_sort", "ksort_sort_batched",
     "ksort_reserve_workspace", "ksort_release_workspace", "ksort_get_device_error",
     "ksort_get_stats", "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
-    "ksort_tile_keys", "ksort_status_string", "ksort_last_cuda_error",
+    "ksort_tile_keys", "ksort_tile_shape", "ksort_status_string", "ksort_last_cuda_error",
     "ksort_selftest_wait_timeout", "ksort_debug_trace",
     "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
 ]
@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("spin_limit_ms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("spin_limit_ms", ctypes.c_int32), ("tile_shape", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -97,6 +97,9 @@ def load():
             "ksort_get_tuning": (i32, [i32, ctypes.POINTER(Tuning)]),
             "ksort_max_cutoff": (i32, [i32]),
             "ksort_tile_keys": (i32, [i32]),
+            "ksort_tile_shape": (i32, [i32, i32, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]),
             "ksort_status_string": (ctypes.c_char_p, [i32]),
             "ksort_last_cuda_error": (ctypes.c_char_p, []),
             "ksort_selftest_wait_timeout": (i32, [i32, vp]),
@@ -204,15 +207,26 @@ def ksort_get_stats(stream=None) -> dict:
     return s.as_dict()
 
 
-def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0):
-    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, 0)
+def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0,
+                     tile_shape: int = 0):
+    """Zero arguments keep their value; ctas_per_sm=-1 restores "as many as fit"."""
+    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape)
     _check(load().ksort_set_tuning(dtype, ctypes.byref(t)), "ksort_set_tuning")
 
 
 def ksort_get_tuning(dtype: int) -> dict:
     t = Tuning()
     _check(load().ksort_get_tuning(dtype, ctypes.byref(t)), "ksort_get_tuning")
-    return {"cutoff": t.cutoff, "ctas_per_sm": t.ctas_per_sm, "spin_limit_ms": t.spin_limit_ms}
+    return {"cutoff": t.cutoff, "ctas_per_sm": t.ctas_per_sm, "spin_limit_ms": t.spin_limit_ms,
+            "tile_shape": t.tile_shape}
+
+
+def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, bool]:
+    """(threads, keys per thread, staged) of partition-pass form `shape` (1-based)."""
+    nt, ipt, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ksort_tile_shape(dtype, shape, ctypes.byref(nt), ctypes.byref(ipt),
+                                   ctypes.byref(st)), "ksort_tile_shape")
+    return int(nt.value), int(ipt.value), bool(st.value)
 
 
 def ksort_max_cutoff(dtype: int) -> int:

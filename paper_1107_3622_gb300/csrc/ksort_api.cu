@@ -36,13 +36,13 @@ bool dtype_ok(int dt) { return dt == KSORT_F32 || dt == KSORT_F64 || dt == KSORT
 
 // ------------------------------------------------------------------ per-type dispatch
 struct Ops {
-  KernelInfo (*info)();
+  KernelInfo (*info)(int);
   size_t (*small_smem_bytes)(int);
-  cudaError_t (*occupancy)(int, int *, int *);
-  cudaError_t (*seed)(const SortParams &, cudaStream_t);
-  cudaError_t (*tiles)(const SortParams &, int, cudaStream_t);
+  cudaError_t (*occupancy)(int, int, int *, int *);
+  cudaError_t (*seed)(const SortParams &, int, cudaStream_t);
+  cudaError_t (*tiles)(const SortParams &, int, int, cudaStream_t);
   cudaError_t (*smalls)(const SortParams &, int, cudaStream_t);
-  long long (*tile_count)(const void *, long long, long long);
+  long long (*tile_count)(int, const void *, long long, long long);
 };
 
 template <typename K>
@@ -62,12 +62,13 @@ struct Tuning {
   int cutoff;
   int ctas_per_sm;  // 0: as many as fit
   int spin_limit_ms;
+  int variant;      // tile shape of the tile passes, 0 .. kTileVariants - 1
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000}, {2048, 0, 2000}, {4096, 0, 2000}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0}, {2048, 0, 2000, 0}, {4096, 0, 2000, 0}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -101,8 +102,8 @@ struct Need {
 // per key, which covers every input (a sort makes at most n - 1 partition calls);
 // beyond that it holds n/32 entries, ~100x what random inputs use. Inputs that need
 // more (near-O(n^2) orders) stop with KSORT_ERR_WORKSPACE_EXHAUSTED.
-Need need_for(ksort_dtype_t dt, long long total, long long arrays) {
-  const KernelInfo ki = ops(dt).info();
+Need need_for(ksort_dtype_t dt, long long total, long long arrays, int variant) {
+  const KernelInfo ki = ops(dt).info(variant);
   const unsigned long long t = (unsigned long long)std::max<long long>(total, 1);
   const unsigned long long a = (unsigned long long)std::max<long long>(arrays, 1);
   unsigned long long items = t <= (1ull << 21) ? t : std::max(1ull << 21, t / 32);
@@ -211,17 +212,18 @@ struct Grids {
   int tiles;   // tile_kernel CTAs filling the GPU
   int smalls;  // small_kernel CTAs filling the GPU
 };
-std::map<std::pair<int, int>, std::pair<int, int>> g_occ;  // (dtype, cutoff) -> CTAs per SM
+// (dtype, variant, cutoff) -> CTAs per SM of (tile_kernel, small_kernel)
+std::map<std::pair<int, int>, std::pair<int, int>> g_occ;
 
 ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g) {
   int sms = 0;
   ksort_status_t st = device_sms(dev, &sms);
   if (st != KSORT_OK) return st;
-  auto key = std::make_pair((int)dt, tu.cutoff);
+  auto key = std::make_pair((int)dt * kTileVariants + tu.variant, tu.cutoff);
   auto it = g_occ.find(key);
   std::pair<int, int> occ;
   if (it == g_occ.end()) {
-    KS_CUDA(ops(dt).occupancy(tu.cutoff, &occ.first, &occ.second));
+    KS_CUDA(ops(dt).occupancy(tu.variant, tu.cutoff, &occ.first, &occ.second));
     g_occ[key] = occ;
   } else {
     occ = it->second;
@@ -276,7 +278,7 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   std::lock_guard<std::mutex> lk(g_mu);
   const Tuning tu = g_tuning[dt];
   Workspace *ws = nullptr;
-  Need need = need_for(dt, n, 1);
+  Need need = need_for(dt, n, 1, tu.variant);
   need.item_cap = 64;
   if (!in_place) need.scratch_bytes = kb;
   st = get_workspace(dev, s, need, &ws);
@@ -288,7 +290,7 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
     return KSORT_OK;
   }
   // One item that only runs Steps 1-4: buffer 0 is read, buffer 1 receives the result.
-  const long long tiles = ops(dt).tile_count(in, 0, n);
+  const long long tiles = ops(dt).tile_count(tu.variant, in, 0, n);
   if ((unsigned long long)tiles > ws->lb_cap) return KSORT_ERR_INVALID_ARG;
   Grids g{};
   if ((st = full_grids(dt, dev, tu, &g)) != KSORT_OK) return st;
@@ -301,8 +303,8 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   p.key_index = reinterpret_cast<long long *>(key_index);
   p.readable[0] = n;
   p.readable[1] = 0;  // buffer 1 is only written
-  KS_CUDA(ops(dt).seed(p, s));
-  KS_CUDA(ops(dt).tiles(p, grid, s));
+  KS_CUDA(ops(dt).seed(p, tu.variant, s));
+  KS_CUDA(ops(dt).tiles(p, tu.variant, grid, s));
   if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
   return KSORT_OK;
 }
@@ -322,13 +324,13 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
   std::lock_guard<std::mutex> lk(g_mu);
   const Tuning tu = g_tuning[dt];
   Workspace *ws = nullptr;
-  st = get_workspace(dev, s, need_for(dt, total, num_arrays), &ws);
+  st = get_workspace(dev, s, need_for(dt, total, num_arrays, tu.variant), &ws);
   if (st != KSORT_OK) return st;
   Grids g{};
   if ((st = full_grids(dt, dev, tu, &g)) != KSORT_OK) return st;
   if (!offsets) {
     // one array: no more CTAs than its first level has tiles, or than small items
-    const KernelInfo ki = ops(dt).info();
+    const KernelInfo ki = ops(dt).info(tu.variant);
     g.tiles = (int)std::max<long long>(
         1, std::min<long long>(g.tiles, (total + ki.tile_keys - 1) / ki.tile_keys));
     g.smalls = (int)std::max<long long>(
@@ -340,8 +342,8 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
   p.total = total;
   p.readable[0] = total;
   p.readable[1] = total + (long long)(kScratchPad / kb);
-  KS_CUDA(ops(dt).seed(p, s));
-  if (offsets || total > tu.cutoff) KS_CUDA(ops(dt).tiles(p, g.tiles, s));
+  KS_CUDA(ops(dt).seed(p, tu.variant, s));
+  if (offsets || total > tu.cutoff) KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
   KS_CUDA(ops(dt).smalls(p, g.smalls, s));
   return KSORT_OK;
 }
@@ -393,7 +395,7 @@ ksort_status_t noalloc_device(int dev, cudaStream_t s, NoallocDevice **out) {
     KS_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     for (int t = 0; t < 3; ++t) {
       int small_ctas = 0;
-      KS_CUDA(ops((ksort_dtype_t)t).occupancy(g_tuning[t].cutoff, &d.tile_ctas[t], &small_ctas));
+      KS_CUDA(ops((ksort_dtype_t)t).occupancy(0, g_tuning[t].cutoff, &d.tile_ctas[t], &small_ctas));
       if (d.tile_ctas[t] < 1) return KSORT_ERR_INTERNAL;
     }
     KS_CUDA(cudaMemsetAsync(base, 0, kNoallocBytes, s));
@@ -435,7 +437,8 @@ ksort_status_t partition_noalloc_impl(ksort_dtype_t dt, const void *in, void *ou
     KS_CUDA(cudaMemcpyAsync(out, in, kb, cudaMemcpyDeviceToDevice, s));
     return KSORT_OK;
   }
-  const long long tiles = ops(dt).tile_count(in, 0, n);
+  // always the default tile shape (variant 0), whatever the tuning says
+  const long long tiles = ops(dt).tile_count(0, in, 0, n);
   if ((unsigned long long)tiles > kNoallocTiles) return KSORT_ERR_TOO_LARGE;
   const Tuning tu = g_tuning[dt];
   unsigned char *b = d->base;
@@ -466,8 +469,8 @@ ksort_status_t partition_noalloc_impl(ksort_dtype_t dt, const void *in, void *ou
   KS_CUDA(cudaMemsetAsync(b + e0, 0, e1 - e0, s));
   const int grid = (int)std::max<long long>(
       1, std::min<long long>((long long)d->sms * d->tile_ctas[dt], tiles));
-  KS_CUDA(ops(dt).seed(p, s));
-  KS_CUDA(ops(dt).tiles(p, grid, s));
+  KS_CUDA(ops(dt).seed(p, 0, s));
+  KS_CUDA(ops(dt).tiles(p, 0, grid, s));
   noalloc_status_kernel<<<1, 1, 0, s>>>(ctl, p.key_index);
   KS_CUDA(cudaGetLastError());
   return KSORT_OK;
@@ -515,7 +518,8 @@ ksort_status_t ksort_reserve_workspace(ksort_dtype_t dtype, int64_t max_total_ke
   if (st != KSORT_OK) return st;
   std::lock_guard<std::mutex> lk(g_mu);
   Workspace *ws = nullptr;
-  st = get_workspace(dev, (cudaStream_t)stream, need_for(dtype, max_total_keys, max_arrays), &ws);
+  st = get_workspace(dev, (cudaStream_t)stream,
+                     need_for(dtype, max_total_keys, max_arrays, g_tuning[dtype].variant), &ws);
   if (st != KSORT_OK) return st;
   Grids g{};  // also warms the occupancy cache (no queries during graph capture)
   return full_grids(dtype, dev, g_tuning[dtype], &g);
@@ -578,25 +582,41 @@ ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out) {
 
 int32_t ksort_max_cutoff(ksort_dtype_t dtype) {
   if (!dtype_ok(dtype)) return 0;
-  return ops(dtype).info().max_cutoff;
+  return ops(dtype).info(0).max_cutoff;
 }
 
 int32_t ksort_tile_keys(ksort_dtype_t dtype) {
   if (!dtype_ok(dtype)) return 0;
-  return ops(dtype).info().tile_keys;
+  std::lock_guard<std::mutex> lk(g_mu);
+  return ops(dtype).info(g_tuning[dtype].variant).tile_keys;
+}
+
+ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
+                                int32_t *keys_per_thread, int32_t *staged) {
+  if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (shape < 1 || shape > kTileVariants || !threads || !keys_per_thread || !staged)
+    return KSORT_ERR_INVALID_ARG;
+  const KernelInfo ki = ops(dtype).info(shape - 1);
+  *threads = ki.block;
+  *keys_per_thread = ki.keys_per_thread;
+  *staged = ki.staged;
+  return KSORT_OK;
 }
 
 ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
   if (!t) return KSORT_ERR_INVALID_ARG;
-  const int maxc = ops(dtype).info().max_cutoff;
+  const int maxc = ops(dtype).info(0).max_cutoff;
   if (t->cutoff < 0 || (t->cutoff > 0 && (t->cutoff < 2 || t->cutoff > maxc))) return KSORT_ERR_INVALID_ARG;
-  if (t->ctas_per_sm < 0 || t->spin_limit_ms < 0) return KSORT_ERR_INVALID_ARG;
+  if (t->ctas_per_sm < -1 || t->spin_limit_ms < 0 || t->spin_limit_ms > 600000)
+    return KSORT_ERR_INVALID_ARG;
+  if (t->tile_shape < 0 || t->tile_shape > kTileVariants) return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
-  if (t->ctas_per_sm) g.ctas_per_sm = t->ctas_per_sm;
+  if (t->ctas_per_sm) g.ctas_per_sm = t->ctas_per_sm < 0 ? 0 : t->ctas_per_sm;
   if (t->spin_limit_ms) g.spin_limit_ms = t->spin_limit_ms;
+  if (t->tile_shape) g.variant = t->tile_shape - 1;
   return KSORT_OK;
 }
 
@@ -608,7 +628,7 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->cutoff = g.cutoff;
   out->ctas_per_sm = g.ctas_per_sm;
   out->spin_limit_ms = g.spin_limit_ms;
-  out->reserved = 0;
+  out->tile_shape = g.variant + 1;
   return KSORT_OK;
 }
 
@@ -627,7 +647,7 @@ ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stre
   if (st != KSORT_OK) return st;
   std::lock_guard<std::mutex> lk(g_mu);
   Workspace *ws = nullptr;
-  Need need = need_for(KSORT_F32, 1, 1);
+  Need need = need_for(KSORT_F32, 1, 1, 0);
   need.item_cap = 64;
   need.scratch_bytes = 4;
   cudaStream_t s = (cudaStream_t)stream;

@@ -24,20 +24,14 @@ namespace ksort {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
-#ifndef KSORT_TILE_THREADS
-#define KSORT_TILE_THREADS 512
-#endif
-constexpr int kTileThreads = KSORT_TILE_THREADS;  // tile_kernel CTA
-constexpr int kTileWarps = kTileThreads / 32;
 constexpr int kSmallThreads = 256;  // small_kernel CTA
 constexpr int kSmallWarps = kSmallThreads / 32;
 
 #ifndef KSORT_LOOKBACK_PER
 #define KSORT_LOOKBACK_PER 1
 #endif
-#ifndef KSORT_TILE_MINB
-#define KSORT_TILE_MINB 2  // tile_kernel CTAs per SM the register budget is sized for
-#endif
+// tile_kernel CTAs per SM that the register budget is sized for (64 registers a thread)
+constexpr int tile_min_blocks(int nt) { return 1024 / nt; }
 
 // ----------------------------------------------------------------------------- PTX
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -769,10 +763,12 @@ __device__ __forceinline__ void trace_mark(const SortParams &p, unsigned long lo
 //   write   less keys of tile t to dst[begin + E ...]; >= keys to the right end,
 //           dst[end - PG - G ...] with PG the >= keys of earlier tiles, so the key's
 //           index begin + #{x < key} stays free.
-// Thread i owns the keys at tile positions (v * kTileThreads + i) * VEC + l. The last
-// tile of an item to finish places the key (Step 4) and queues both sides (Steps 5-6).
+// Thread i owns the keys at tile positions (v * NT + i) * VEC + l. The last tile of an
+// item to finish places the key (Step 4) and queues both sides (Steps 5-6). The tile
+// shape (NT threads x IPT keys) is one of a few compiled variants picked at run time.
+template <int NW>
 struct TileCtaShared {
-  unsigned wl[kTileWarps], wg[kTileWarps];
+  unsigned wl[NW], wg[NW];
   unsigned long long E;
   int abort;
   int r;        // ticket status for the CTA
@@ -787,17 +783,16 @@ struct TileCtaShared {
   unsigned ctiles[2];
 };
 
-template <typename K, int IPT>
-__global__ void __launch_bounds__(kTileThreads, KSORT_TILE_MINB) tile_kernel(SortParams p) {
-  constexpr int NT = kTileThreads;
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParams p) {
   constexpr int TILE = NT * IPT;
   constexpr int VEC = Vec<K>::N;
   constexpr int NV = IPT / VEC;
-  constexpr int NW = kTileWarps;
-  static_assert(IPT % VEC == 0 && IPT <= 32, "bad tile shape");
+  constexpr int NW = NT / 32;
+  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0, "bad tile shape");
   using V = typename Vec<K>::T;
   __shared__ __align__(16) K sout[TILE];
-  __shared__ TileCtaShared sh;
+  __shared__ TileCtaShared<NW> sh;
   K *const buf0 = static_cast<K *>(p.keys);
   K *const buf1 = static_cast<K *>(p.scratch);
   Control *ctl = p.ctl;
@@ -1020,6 +1015,425 @@ __global__ void __launch_bounds__(kTileThreads, KSORT_TILE_MINB) tile_kernel(Sor
       }
     }
     if (tid == 0) trace_mark(p, sh.k, 6);  // completed
+  }
+  if (tid == 0) {
+    if (st_tiles) atomicAdd(&ctl->tiles, st_tiles);
+    if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
+    if (st_large) atomicAdd(&ctl->large_items, st_large);
+    if (st_large_keys) atomicAdd(&ctl->large_keys, st_large_keys);
+  }
+}
+
+// ----------------------------------------------------------------------------- staged
+// Bulk copies global -> shared (cp.async.bulk) with mbarrier completion.
+__device__ __forceinline__ unsigned smem_u32(const void *ptr) {
+  return (unsigned)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of `bar` to complete; false if limit_ns passed first.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (unsigned i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 31u) == 0u && globaltimer() - t0 > limit_ns) return false;
+  }
+}
+
+// Geometry of one tile pass, written by thread 0 into shared memory.
+struct PipeTile {
+  Item it;
+  long long h;              // item index
+  long long lo;             // first buffer index of the tile (16-byte aligned)
+  unsigned long long k;     // ticket
+  unsigned t;               // tile index within the item
+  int vlo, vhi;             // classified keys of the tile: [vlo, vhi)
+  int agg;                  // aggregate already published
+};
+
+template <int NW>
+struct PipeCtaShared {
+  unsigned wl[NW], wg[NW];
+  unsigned long long E;
+  int abort;
+  int last;
+  int r;          // status of the ticket the CTA waited for
+  int next;       // next tile: 1 claimed but not yet issued, 2 issued and being copied
+  int fail;       // the early count gave up waiting for the next tile's keys
+  unsigned early_L;
+  long long ch;   // item whose record is cached in `ci`
+  Item ci;
+  PipeTile cur, nxt;
+  unsigned long long cidx[2], ct0[2];
+  unsigned ctiles[2];
+  unsigned long long bar[2];
+};
+
+template <typename K, int TILE>
+__device__ __forceinline__ void pipe_geom(const SortParams &p, PipeTile &pt, Item *ci,
+                                          long long *ch, unsigned long long k, long long h) {
+  if (h != *ch) {
+    load_item(p.items + h, ci);
+    *ch = h;
+  }
+  pt.it = *ci;
+  const K *src = static_cast<const K *>((pt.it.flags & kItemScratch) ? p.scratch : p.keys);
+  pt.k = k;
+  pt.h = h;
+  pt.t = (unsigned)(k - pt.it.lb);
+  pt.lo = tile_base(src, pt.it.begin) + (long long)pt.t * TILE;
+  const long long first = pt.it.begin + 1;
+  pt.vlo = (int)(first > pt.lo ? first - pt.lo : 0);
+  pt.vhi = (int)(pt.it.end - pt.lo < TILE ? pt.it.end - pt.lo : TILE);
+  pt.agg = 0;
+}
+
+// One bulk copy of the tile's keys, rounded out to whole 16-byte blocks (they hold
+// classified keys, so the copy stays inside the buffer's allocation).
+template <typename K>
+__device__ __forceinline__ void pipe_issue(const SortParams &p, const PipeTile &pt, K *sdst,
+                                           unsigned long long *bar) {
+  constexpr int VEC = Vec<K>::N;
+  const K *src = static_cast<const K *>((pt.it.flags & kItemScratch) ? p.scratch : p.keys);
+  const unsigned bytes = (unsigned)((pt.vhi + VEC - 1) / VEC * VEC) * (unsigned)sizeof(K);
+  fence_proxy_async();  // earlier generic writes of the keys before the async-proxy read
+  mbar_expect_tx(bar, bytes);
+  bulk_g2s(sdst, src + pt.lo, bytes, bar);
+}
+
+template <typename K, int TILE>
+constexpr size_t pipe_smem_bytes() { return (size_t)3 * TILE * sizeof(K); }
+
+// Phase 1, staged form of tile_kernel: the same tile passes, Steps and output, with the
+// next tile overlapped. Right after the current tile's keys arrive, thread 0 claims the
+// next ticket; if that ticket is already issued, its keys start streaming into the
+// second shared-memory buffer by one bulk copy. While warp 0 runs the current tile's
+// look-back, the other warps scatter and then count the next tile in shared memory and
+// publish its aggregate as soon as its keys land, so later tiles' look-backs do not
+// wait for this CTA. A claimed ticket that is not issued yet is waited for only after
+// the current tile is complete (its completion may be what issues it).
+// Dynamic shared memory: two input tiles and the output tile.
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(SortParams p) {
+  constexpr int TILE = NT * IPT;
+  constexpr int VEC = Vec<K>::N;
+  constexpr int NV = IPT / VEC;
+  constexpr int NW = NT / 32;
+  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0 && NW > 1, "bad tile shape");
+  using V = typename Vec<K>::T;
+  extern __shared__ __align__(128) unsigned char pipe_smem[];
+  K *const sin0 = reinterpret_cast<K *>(pipe_smem);
+  K *const sout = sin0 + 2 * TILE;
+  __shared__ PipeCtaShared<NW> sh;
+  K *const buf0 = static_cast<K *>(p.keys);
+  K *const buf1 = static_cast<K *>(p.scratch);
+  Control *ctl = p.ctl;
+  const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  unsigned long long st_tiles = 0, st_lb = 0, st_large = 0, st_large_keys = 0;
+  unsigned phase = 0;  // bit j: parity of the next completion of buffer j
+  int b = 0;           // buffer of the current tile
+
+  if (tid == 0) {
+    mbar_init(&sh.bar[0], 1);
+    mbar_init(&sh.bar[1], 1);
+    fence_mbar_init();
+    sh.ch = -1;
+    sh.next = 0;
+    const unsigned long long k = atomicAdd(&ctl->tq_head, 1ull);
+    trace_mark(p, k, 0);  // claimed
+    long long h = 0;
+    const int r = wait_ticket(p, epoch, k, &h);
+    sh.r = r;
+    if (r > 0) {
+      pipe_geom<K, TILE>(p, sh.cur, &sh.ci, &sh.ch, k, h);
+      pipe_issue<K>(p, sh.cur, sin0, &sh.bar[0]);
+      trace_mark(p, k, 1);  // copy issued
+    }
+  }
+  __syncthreads();
+  if (sh.r <= 0) return;
+
+  while (true) {
+    // ---- the current tile's keys (copy issued earlier into buffer b)
+    const bool landed = mbar_wait(&sh.bar[b], (phase >> b) & 1u, p.spin_limit_ns);
+    phase ^= 1u << b;
+    K *const sin = sin0 + b * TILE;
+    K *const snx = sin0 + (b ^ 1) * TILE;
+
+    // ---- thread 0: claim the next ticket; start its copy if it is issued already
+    if (tid == 0) {
+      sh.early_L = 0;
+      sh.fail = 0;
+      const unsigned long long kn = atomicAdd(&ctl->tq_head, 1ull);
+      trace_mark(p, kn, 0);  // claimed
+      sh.nxt.k = kn;
+      int state = 1;
+      if (kn < p.lb_cap) {
+        const unsigned long long v = ld_acquire(&p.tmap[kn]);
+        if ((unsigned)(v >> 32) == epoch) {
+          pipe_geom<K, TILE>(p, sh.nxt, &sh.ci, &sh.ch, kn, (long long)(v & 0xffffffffull));
+          pipe_issue<K>(p, sh.nxt, snx, &sh.bar[b ^ 1]);
+          trace_mark(p, kn, 1);  // copy issued
+          state = 2;
+        }
+      }
+      sh.next = state;
+    }
+
+    const int vlo = sh.cur.vlo, vhi = sh.cur.vhi;
+    const unsigned t = sh.cur.t;
+    const Item it = sh.cur.it;
+    const long long lo = sh.cur.lo, h = sh.cur.h;
+    const unsigned par = it.flags & kItemScratch;
+    K *dst = par ? buf0 : buf1;
+    const K key = bits_key<K>(it.key);  // Step 1: the first element is the key
+
+    // ---- count (Step 3) from shared memory
+    K x[IPT];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const V q = *reinterpret_cast<const V *>(sin + (v * NT + tid) * VEC);
+      if constexpr (VEC == 4) {
+        x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
+      } else {
+        x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
+      }
+    }
+    unsigned lessbits = 0, gebits = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        const int j = v * VEC + l, kk = (v * NT + tid) * VEC + l;
+        const bool valid = kk >= vlo && kk < vhi;
+        const bool le = goes_left(key, x[j]);
+        lessbits |= (unsigned)(valid && le) << j;
+        gebits |= (unsigned)(valid && !le) << j;
+      }
+    }
+    const unsigned mine = (unsigned)__popc(lessbits) | ((unsigned)__popc(gebits) << 16);
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) {
+      sh.wl[w] = incl & 0xffffu;
+      sh.wg[w] = incl >> 16;
+    }
+    if (__syncthreads_or(!landed)) {
+      // the copy did not land in time: record it, let it finish (bounded), stop
+      if (tid == 0) raise_error(ctl, kDevTimeout, 0x800000000ull | t);
+      mbar_wait(&sh.bar[b], ((phase >> b) & 1u) ^ 1u, p.spin_limit_ns);
+      if (sh.next == 2) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+      break;
+    }
+    unsigned L = 0, G = 0, wlx = 0, wgx = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      const unsigned a = sh.wl[i], c = sh.wg[i];
+      if (i < w) {
+        wlx += a;
+        wgx += c;
+      }
+      L += a;
+      G += c;
+    }
+    unsigned long long *lb = p.lb + it.lb;
+    if (tid == 0) {
+      if (!sh.cur.agg) st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));
+      trace_mark(p, sh.cur.k, 2);
+    }
+
+    // ---- look-back (warp 0); scatter (all); early count of the next tile (warps 1..)
+    if (w == 0) {
+      unsigned long long E = 0;
+      int status = 0;
+      if (t > 0) {
+        unsigned long long steps = 0;
+        status = lookback(lb, t, epoch, p.spin_limit_ns, &ctl->abort, &E, &steps);
+        if (lane == 0) {
+          if (status == 0) st_relaxed(&lb[t], lb_pack(epoch, true, (unsigned)(E + L)));
+          st_lb += steps;
+        }
+      }
+      if (lane == 0) {
+        if (status == 1) raise_error(ctl, kDevTimeout, 0x100000000ull | t);
+        sh.E = E;
+        sh.abort = status == 0 ? 0 : 1;
+        trace_mark(p, sh.cur.k, 3);
+      }
+    }
+    {
+      const unsigned excl = incl - mine;
+      unsigned rl = wlx + (excl & 0xffffu);
+      unsigned rg = L + wgx + (excl >> 16);
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if ((lessbits >> j) & 1u) sout[rl++] = x[j];
+        else if ((gebits >> j) & 1u) sout[rg++] = x[j];
+      }
+    }
+    if (w > 0 && sh.next == 2) {
+      const bool ok = mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+      if (__all_sync(kFull, ok)) {
+        const int nlo = sh.nxt.vlo, nhi = sh.nxt.vhi;
+        const K nkey = bits_key<K>(sh.nxt.it.key);
+        unsigned cnt = 0;
+        for (int v = tid - 32; v < TILE / VEC; v += NT - 32) {
+          const V q = *reinterpret_cast<const V *>(snx + v * VEC);
+          K y[VEC];
+          if constexpr (VEC == 4) {
+            y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
+          } else {
+            y[0] = q.x; y[1] = q.y;
+          }
+#pragma unroll
+          for (int l = 0; l < VEC; ++l) {
+            const int kk = v * VEC + l;
+            cnt += (kk >= nlo && kk < nhi && goes_left(nkey, y[l])) ? 1u : 0u;
+          }
+        }
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (lane == 0) atomicAdd(&sh.early_L, cnt);
+      } else if (lane == 0) {
+        sh.fail = 1;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");
+      if (tid == 32 && !sh.fail) {
+        st_relaxed(&p.lb[sh.nxt.it.lb + sh.nxt.t], lb_pack(epoch, sh.nxt.t == 0, sh.early_L));
+        sh.nxt.agg = 1;
+        trace_mark(p, sh.nxt.k, 5);  // aggregate published early
+      }
+    }
+    __syncthreads();
+    const unsigned long long E = sh.E;
+    if (sh.abort) {
+      if (sh.next == 2) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+      break;
+    }
+
+    // ---- write
+    long long lbase = 0, gbase = 0;
+    if (!tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase)) {
+      if (tid == 0) raise_error(ctl, kDevInternal, 0x500000000ull | t);
+      if (sh.next == 2) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+      break;
+    }
+    copy_out<K, NT>(sout, dst + lbase, L);
+    copy_out<K, NT>(sout + L, dst + gbase, G);
+    __syncthreads();
+
+    // ---- completion: the last tile of the item places the key and queues both sides
+    if (tid == 0) {
+      trace_mark(p, sh.cur.k, 4);
+      ++st_tiles;
+      if (t == it.tiles - 1) atomicExch(&p.ictl[h].less, E + L);
+      const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);
+      sh.last = done_before == it.tiles - 1;
+      sh.ctiles[0] = sh.ctiles[1] = 0;
+      if (sh.last) {
+        __threadfence();
+        const unsigned long long c = ld_acquire(&p.ictl[h].less);
+        const long long kpos = it.begin + (long long)c;
+        if (kpos >= it.end) {
+          raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)h);
+        } else if (it.flags & kItemPartitionOnly) {
+          dst[kpos] = key;
+          if (p.key_index) *p.key_index = (long long)c;
+        } else {
+          buf0[kpos] = key;  // Step 4
+          const unsigned cflags = par ^ kItemScratch;
+          const long long cb[2] = {it.begin, kpos + 1};
+          const long long ce[2] = {kpos, it.end};
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {  // Steps 5-6
+            const long long mm = ce[s] - cb[s];
+            if (mm == 1) {
+              if (cflags & kItemScratch) buf0[cb[s]] = __ldcg(dst + cb[s]);
+            } else if (mm >= 2) {
+              unsigned long long t0 = 0;
+              unsigned tiles = 0;
+              sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb[s], ce[s], cflags, &t0, &tiles);
+              sh.ct0[s] = t0;
+              sh.ctiles[s] = tiles;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (sh.last) {
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        if (sh.ctiles[s]) publish_tickets(p, epoch, sh.cidx[s], sh.ct0[s], sh.ctiles[s], tid, NT);
+      __syncthreads();
+      if (tid == 0) {
+        ++st_large;
+        st_large_keys += (unsigned long long)(it.end - it.begin);
+        __threadfence();
+        atomicAdd(&ctl->large_completed, 1ull);
+      }
+    }
+
+    // ---- advance: the next tile becomes current (waiting for its ticket if needed)
+    if (tid == 0) {
+      trace_mark(p, sh.cur.k, 6);
+      if (p.trace && sh.cur.k < (unsigned long long)p.trace_cap)
+        p.trace[sh.cur.k * kTraceWords + 7] = blockIdx.x;
+      if (sh.next == 2) {
+        sh.cur = sh.nxt;
+        sh.r = 1;
+      } else {
+        long long hn = 0;
+        const int r = wait_ticket(p, epoch, sh.nxt.k, &hn);
+        sh.r = r;
+        if (r > 0) {
+          pipe_geom<K, TILE>(p, sh.cur, &sh.ci, &sh.ch, sh.nxt.k, hn);
+          pipe_issue<K>(p, sh.cur, snx, &sh.bar[b ^ 1]);
+          trace_mark(p, sh.nxt.k, 1);  // copy issued
+        }
+      }
+    }
+    __syncthreads();
+    if (sh.r <= 0) break;
+    b ^= 1;
   }
   if (tid == 0) {
     if (st_tiles) atomicAdd(&ctl->tiles, st_tiles);

@@ -90,22 +90,30 @@ struct SortParams {
 };
 constexpr int kTraceWords = 8;
 
-// Host-side launch interface, one explicit instantiation per key type.
+// Host-side launch interface, one explicit instantiation per key type. `variant`
+// selects one of kTileVariants compiled forms of the tile passes: three tile shapes
+// (variants 0-2) of tile_kernel, and the same shapes staged through shared memory by
+// bulk copies (variants 3-5, tile_pipe_kernel).
+constexpr int kTileShapes = 3;
+constexpr int kTileVariants = 2 * kTileShapes;
+
 struct KernelInfo {
   int block;          // threads per tile-pass CTA
   int tile_keys;      // keys per tile pass
   int max_cutoff;     // largest shared-memory item the kernels support
+  int keys_per_thread;
+  int staged;         // 1: tile_pipe_kernel
 };
 
 template <typename K>
 struct Launcher {
-  static KernelInfo info();
+  static KernelInfo info(int variant);
   static size_t small_smem_bytes(int cutoff);
-  static cudaError_t occupancy(int cutoff, int *tile_ctas, int *small_ctas);
-  static cudaError_t seed(const SortParams &p, cudaStream_t s);
-  static cudaError_t tiles(const SortParams &p, int grid, cudaStream_t s);
+  static cudaError_t occupancy(int variant, int cutoff, int *tile_ctas, int *small_ctas);
+  static cudaError_t seed(const SortParams &p, int variant, cudaStream_t s);
+  static cudaError_t tiles(const SortParams &p, int variant, int grid, cudaStream_t s);
   static cudaError_t smalls(const SortParams &p, int grid, cudaStream_t s);
-  static long long tile_count(const void *buf, long long begin, long long end);
+  static long long tile_count(int variant, const void *buf, long long begin, long long end);
 };
 
 }  // namespace ksort

@@ -6,18 +6,75 @@
 
 namespace ksort {
 
-// Keys per thread of a tile pass: a tile is kTileThreads * IPT keys (8 KiB).
-template <typename K> struct Shape;
-template <> struct Shape<float> { static constexpr int IPT = 16; };
-template <> struct Shape<unsigned> { static constexpr int IPT = 16; };
-template <> struct Shape<double> { static constexpr int IPT = 8; };
+// Compiled tile shapes (threads x keys per thread) of the tile passes, picked at run
+// time by the tuning's tile shape; every shape moves 128-bit vectors. Variant 0 is the
+// default: 32 KiB tiles of 512 threads.
+template <typename K> struct Shapes;
+template <> struct Shapes<float> {
+  static constexpr int NT[kTileShapes] = {512, 512, 256};
+  static constexpr int IPT[kTileShapes] = {16, 8, 16};
+};
+template <> struct Shapes<unsigned> {
+  static constexpr int NT[kTileShapes] = {512, 512, 256};
+  static constexpr int IPT[kTileShapes] = {16, 8, 16};
+};
+template <> struct Shapes<double> {
+  static constexpr int NT[kTileShapes] = {512, 512, 256};
+  static constexpr int IPT[kTileShapes] = {8, 4, 8};
+};
+
+// Variant V: shape V % kTileShapes, staged through shared memory when V >= kTileShapes.
+template <typename K, int V>
+struct ShapeOf {
+  static constexpr int NT = Shapes<K>::NT[V % kTileShapes];
+  static constexpr int IPT = Shapes<K>::IPT[V % kTileShapes];
+  static constexpr int TILE = NT * IPT;
+  static constexpr bool STAGED = V >= kTileShapes;
+  static constexpr size_t SMEM = STAGED ? dev::pipe_smem_bytes<K, TILE>() : 0;
+};
+
+// Calls f(ShapeOf<K, v>{}) for the run-time variant v (out-of-range values: variant 0).
+template <typename K, typename F>
+decltype(auto) with_shape(int v, F &&f) {
+  switch (v) {
+    case 1: return f(ShapeOf<K, 1>{});
+    case 2: return f(ShapeOf<K, 2>{});
+    case 3: return f(ShapeOf<K, 3>{});
+    case 4: return f(ShapeOf<K, 4>{});
+    case 5: return f(ShapeOf<K, 5>{});
+    default: return f(ShapeOf<K, 0>{});
+  }
+}
+
+// The tile-pass kernel of a variant, with its dynamic shared memory allowed.
+template <typename K, typename S>
+cudaError_t tile_kernel_of(void (**fn)(SortParams)) {
+  if constexpr (S::STAGED) {
+    *fn = dev::tile_pipe_kernel<K, S::NT, S::IPT>;
+    cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+  } else {
+    *fn = dev::tile_kernel<K, S::NT, S::IPT>;
+    return cudaSuccess;
+  }
+}
+
+// Largest shared-memory cutoff: two staging buffers of cutoff keys must fit in one
+// CTA's shared memory (227 KB), so 8-byte keys stop at half the 4-byte limit.
+template <typename K>
+constexpr int max_cutoff() { return sizeof(K) == 8 ? dev::kMaxSmallCutoff / 2 : dev::kMaxSmallCutoff; }
+static_assert(dev::small_smem_bytes<double>(max_cutoff<double>()) <= 227 * 1024, "smem");
+static_assert(dev::small_smem_bytes<float>(max_cutoff<float>()) <= 227 * 1024, "smem");
 
 template <typename K>
-constexpr int tile_keys() { return dev::kTileThreads * Shape<K>::IPT; }
-
-template <typename K>
-KernelInfo Launcher<K>::info() {
-  return KernelInfo{dev::kTileThreads, tile_keys<K>(), dev::kMaxSmallCutoff};
+KernelInfo Launcher<K>::info(int variant) {
+  return with_shape<K>(variant, [](auto s) {
+    using S = decltype(s);
+    return KernelInfo{S::NT, S::TILE, max_cutoff<K>(), S::IPT, S::STAGED ? 1 : 0};
+  });
 }
 
 template <typename K>
@@ -26,14 +83,22 @@ size_t Launcher<K>::small_smem_bytes(int cutoff) {
 }
 
 template <typename K>
-long long Launcher<K>::tile_count(const void *buf, long long begin, long long end) {
-  return dev::tile_count<K, tile_keys<K>()>(static_cast<const K *>(buf), begin, end);
+long long Launcher<K>::tile_count(int variant, const void *buf, long long begin, long long end) {
+  return with_shape<K>(variant, [&](auto s) {
+    using S = decltype(s);
+    return (long long)dev::tile_count<K, S::TILE>(static_cast<const K *>(buf), begin, end);
+  });
 }
 
 template <typename K>
-cudaError_t Launcher<K>::occupancy(int cutoff, int *tile_ctas, int *small_ctas) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      tile_ctas, dev::tile_kernel<K, Shape<K>::IPT>, dev::kTileThreads, 0);
+cudaError_t Launcher<K>::occupancy(int variant, int cutoff, int *tile_ctas, int *small_ctas) {
+  cudaError_t e = with_shape<K>(variant, [&](auto s) {
+    using S = decltype(s);
+    void (*fn)(SortParams) = nullptr;
+    cudaError_t e2 = tile_kernel_of<K, S>(&fn);
+    if (e2 != cudaSuccess) return e2;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(tile_ctas, fn, S::NT, S::SMEM);
+  });
   if (e != cudaSuccess) return e;
   auto sk = dev::small_kernel<K>;
   const size_t smem = small_smem_bytes(cutoff);
@@ -43,15 +108,25 @@ cudaError_t Launcher<K>::occupancy(int cutoff, int *tile_ctas, int *small_ctas) 
 }
 
 template <typename K>
-cudaError_t Launcher<K>::seed(const SortParams &p, cudaStream_t s) {
-  dev::seed_kernel<K, tile_keys<K>()><<<1, 1024, 0, s>>>(p);
+cudaError_t Launcher<K>::seed(const SortParams &p, int variant, cudaStream_t st) {
+  with_shape<K>(variant, [&](auto s) {
+    using S = decltype(s);
+    dev::seed_kernel<K, S::TILE><<<1, 1024, 0, st>>>(p);
+    return 0;
+  });
   return cudaGetLastError();
 }
 
 template <typename K>
-cudaError_t Launcher<K>::tiles(const SortParams &p, int grid, cudaStream_t s) {
-  dev::tile_kernel<K, Shape<K>::IPT><<<grid, dev::kTileThreads, 0, s>>>(p);
-  return cudaGetLastError();
+cudaError_t Launcher<K>::tiles(const SortParams &p, int variant, int grid, cudaStream_t st) {
+  return with_shape<K>(variant, [&](auto s) {
+    using S = decltype(s);
+    void (*fn)(SortParams) = nullptr;
+    cudaError_t e = tile_kernel_of<K, S>(&fn);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, S::NT, S::SMEM, st>>>(p);
+    return cudaGetLastError();
+  });
 }
 
 template <typename K>

@@ -88,3 +88,43 @@ def test_oracle_and_library_share_no_code():
         if os.path.isfile(path) and path.endswith((".py", ".c", ".h")):
             text = open(path).read()
             assert "paper_1107_3622_gb300" not in text and "ksort.h" not in text, path
+
+
+def test_tile_shapes_and_tuning_fields(lib):
+    import paper_1107_3622_gb300 as ks
+    for code in (ks.F32, ks.F64, ks.U32):
+        shapes = [ks.ksort_tile_shape(code, s) for s in range(1, 7)]
+        vec = 2 if code == ks.F64 else 4
+        for nt, ipt, _ in shapes:
+            assert nt % 32 == 0 and ipt % vec == 0 and ipt <= 32
+        assert len(set(shapes)) == 6
+        assert [st for _, _, st in shapes] == [False] * 3 + [True] * 3
+        assert [s[:2] for s in shapes[:3]] == [s[:2] for s in shapes[3:]]
+        with pytest.raises(ks.KSortError):
+            ks.ksort_tile_shape(code, 0)
+        with pytest.raises(ks.KSortError):
+            ks.ksort_tile_shape(code, 7)
+        before = ks.ksort_get_tuning(code)
+        assert before["tile_shape"] in range(1, 7)
+        with pytest.raises(ks.KSortError):
+            ks.ksort_set_tuning(code, tile_shape=7)
+        with pytest.raises(ks.KSortError):
+            ks.ksort_set_tuning(code, ctas_per_sm=-2)
+        ks.ksort_set_tuning(code, tile_shape=2)
+        nt, ipt, _ = shapes[1]
+        assert ks.ksort_tile_keys(code) == nt * ipt
+        ks.ksort_set_tuning(code, tile_shape=before["tile_shape"])
+        assert ks.ksort_get_tuning(code) == before
+    # shared-memory staging of two cutoff-sized buffers must fit a CTA (227 KB)
+    assert 2 * 8 * ks.ksort_max_cutoff(ks.F64) <= 227 * 1024
+    assert 2 * 4 * ks.ksort_max_cutoff(ks.F32) <= 227 * 1024
+
+
+def test_autotune_workload_keys():
+    import numpy as np
+    from paper_1107_3622_gb300 import autotune
+    assert autotune.workload_key("sort", 0, n=7_000_000) == "sort:f32:2^23"
+    assert autotune.workload_key("sort", 1, n=1_000_000) == "sort:f64:2^20"
+    k = autotune.workload_key("batched", 2, lengths=np.array([100, 1000, 500_000]))
+    assert k == "batched:u32:3x[100,500000]:2^19"
+    assert len(autotune.library_hash()) == 16

@@ -1,0 +1,111 @@
+"""Every tuning the autotuner may pick keeps GPU results bit-identical to the oracle:
+each compiled tile shape of the partition passes (sort and first-level partition),
+cutoffs at both ends of their range, and a capped finisher. Then the autotuner itself:
+it searches, applies its choice, caches it, and a second call reads the cache."""
+import numpy as np
+import pytest
+
+import ksort_inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = {"f32": 0, "f64": 1, "u32": 2}
+
+
+@pytest.fixture(scope="module")
+def ks():
+    import torch
+    import paper_1107_3622_gb300 as ks
+    ks.load()
+    torch.cuda.set_device(0)
+    return ks
+
+
+@pytest.fixture
+def restore(ks):
+    saved = {c: ks.ksort_get_tuning(c) for c in DTYPES.values()}
+    yield
+    for c, t in saved.items():
+        ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
+                            tile_shape=t["tile_shape"])
+
+
+def _sort(ks, a):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ks.sort_(t)
+    assert ks.ksort_get_device_error() == 0
+    return t.cpu().numpy()
+
+
+def _oracle(ref, a):
+    b = a.copy()
+    ref.sort(b)
+    return b
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("dtype", list(DTYPES))
+def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
+    import torch
+    code = DTYPES[dtype]
+    ks.ksort_set_tuning(code, tile_shape=shape)
+    nt, ipt, _ = ks.ksort_tile_shape(code, shape)
+    assert ks.ksort_tile_keys(code) == nt * ipt
+    tile = nt * ipt
+    for n in (tile - 1, tile + 1, 3 * tile + 5, 250_003):
+        a = gen.make("uniform", dtype, n, gen.seed_for(6, shape, n % 1009))
+        assert _sort(ks, a).tobytes() == _oracle(ref, a).tobytes()
+        t = torch.from_numpy(a).cuda()
+        i = ks.partition_(t)
+        b = a.copy()
+        ri, *_ = ref.partition(b)
+        got = t.cpu().numpy()
+        assert i == ri and got[i] == a[0]
+        assert np.sort(got[:i]).tobytes() == np.sort(b[:ri]).tobytes()
+        assert np.sort(got[i + 1:]).tobytes() == np.sort(b[ri + 1:]).tobytes()
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
+def test_tile_shapes_batched(ref, ks, restore, shape):
+    import torch
+    ks.ksort_set_tuning(0, tile_shape=shape)
+    lengths = gen.batched_lengths(64, 2, 60_000, seed=gen.seed_for(6, 9, shape))
+    off = gen.offsets_from_lengths(lengths)
+    a = gen.uniform_f32(gen.seed_for(6, 10, shape), int(off[-1]))
+    t = torch.from_numpy(a).cuda()
+    ks.sort_batched_(t, torch.from_numpy(off).cuda())
+    got = t.cpu().numpy()
+    assert ks.ksort_get_device_error() == 0
+    for r in range(len(lengths)):
+        seg = a[off[r]:off[r + 1]]
+        assert got[off[r]:off[r + 1]].tobytes() == _oracle(ref, seg).tobytes()
+
+
+@pytest.mark.parametrize("cutoff,ctas", [(2, 0), (16384, -1), (1024, 1)])
+def test_cutoff_and_finisher_extremes(ref, ks, restore, cutoff, ctas):
+    for dtype, code in DTYPES.items():
+        c = min(cutoff, ks.ksort_max_cutoff(code))
+        ks.ksort_set_tuning(code, cutoff=c, ctas_per_sm=ctas)
+        for pattern in ("uniform", "distinct16"):
+            a = gen.make(pattern, dtype, 40_000, gen.seed_for(6, 11, c))
+            assert _sort(ks, a).tobytes() == _oracle(ref, a).tobytes(), (dtype, pattern)
+
+
+def test_autotuner_searches_applies_and_caches(ks, restore, tmp_path, monkeypatch):
+    from paper_1107_3622_gb300 import autotune
+    monkeypatch.setenv("KSORT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    e = autotune.autotune("sort", ks.F32, n=300_000, reps=2, max_rounds=1)
+    assert not e["cached"] and e["ms"] > 0
+    t = ks.ksort_get_tuning(ks.F32)
+    assert t["tile_shape"] == e["tuning"]["tile_shape"]
+    assert t["cutoff"] == e["tuning"]["cutoff"]
+    assert len(e["candidates"]) >= len(autotune.SHAPES)
+    assert min(c["ms"] for c in e["candidates"]) == pytest.approx(e["ms"])
+    autotune.reset(ks.F32)
+    e2 = autotune.autotune("sort", ks.F32, n=300_000)
+    assert e2["cached"] and e2["tuning"] == e["tuning"]
+    assert ks.ksort_get_tuning(ks.F32)["tile_shape"] == e["tuning"]["tile_shape"]
+    lengths = gen.batched_lengths(128, 100, 100_000, seed=gen.seed_for(6, 12, 0))
+    eb = autotune.autotune("batched", ks.F32, lengths=lengths, reps=2, max_rounds=1)
+    assert eb["workload"].startswith("batched:f32:128x")
