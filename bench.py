@@ -291,7 +291,7 @@ def autotune_sort(ks, n: int, args) -> dict:
     e = autotune.autotune("sort", ks.F32, n=n, reps=3)
     shape = ks.ksort_tile_shape(ks.F32, e["tuning"]["tile_shape"])
     return dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
-                keys_per_thread=shape[1], staged=shape[2], search_ms=e["ms"],
+                keys_per_thread=shape[1], form=shape[2], search_ms=e["ms"],
                 candidates=len(e.get("candidates", [])), cached=e["cached"])
 
 
@@ -396,7 +396,7 @@ def run_ours(args, dist: Dist):
     extras = set() if args.no_extras else {x.strip() for x in args.extras.split(",") if x.strip()}
     if dist.rank == 0:
         if "partition" in extras:
-            line["partition_pass"] = run_partition_pass(ks, n, peak, peak_src)
+            line["partition_pass"] = run_partition_pass(ks, n, peak, peak_src, args)
         if "batched" in extras:
             line["batched"] = run_batched(ks, args)
         if "serving" in extras and args.serving_requests > 0:
@@ -438,9 +438,22 @@ def run_e2e(ks, host, args, stream):
             "path": "pinned host -> cudaMemcpyAsync -> ksort_sort -> cudaMemcpyAsync -> host"}
 
 
-def run_partition_pass(ks, n, peak, peak_src):
-    """ksort_partition_out alone: rotating over 8 input/output pairs (> L2 in total)."""
+def run_partition_pass(ks, n, peak, peak_src, args):
+    """ksort_partition_out alone (autotuned form): rotating over 8 input/output pairs
+    (> L2 in total)."""
     import torch
+    from paper_1107_3622_gb300 import autotune
+    saved = ks.ksort_get_tuning(ks.F32)
+    if args.no_autotune:
+        autotune.reset(ks.F32)
+        tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=False)
+    else:
+        e = autotune.autotune("partition", ks.F32, n=n, reps=5)
+        shape = ks.ksort_tile_shape(ks.F32, e["tuning"]["tile_shape"])
+        tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
+                     keys_per_thread=shape[1], form=shape[2], search_ms=e["ms"],
+                     cached=e["cached"])
+    ks.ksort_reserve_workspace(ks.F32, n, 1)
     R, reps = 8, 20
     ins = [torch.from_numpy(gen.uniform_f32(gen.seed_for(1, 6, 500 + r), n)).cuda()
            for r in range(R)]
@@ -465,7 +478,10 @@ def run_partition_pass(ks, n, peak, peak_src):
     o = outs[0]
     assert float(o[i]) == float(ins[0][0])
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
-    return {"kernel": "ksort_partition_out: seed_kernel + tile_kernel<float>", "n": n,
+    ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
+                        tile_shape=saved["tile_shape"])
+    return {"kernel": "ksort_partition_out: seed_kernel + tile-pass kernel of the tuned form",
+            "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),
             "peak_source": f"{peak_src} hbm_gbs",

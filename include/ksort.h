@@ -156,7 +156,7 @@ KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *o
  *   ctas_per_sm:   shared-memory finisher CTAs per SM (capped by occupancy);
  *                  -1 = as many as fit (the default);
  *   spin_limit_ms: time limit of every device-side wait (1 .. 600000);
- *   tile_shape:    form of the partition passes, 1 .. 6 (1 = default); see
+ *   tile_shape:    form of the partition passes, 1 .. 9 (1 = default); see
  *                  ksort_tile_shape(). Changing it may grow a stream's workspace on
  *                  the next call, so reserve again before capturing a graph.
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
@@ -174,13 +174,17 @@ KSORT_API int32_t ksort_max_cutoff(ksort_dtype_t dtype);
  * tuning (threads x keys per thread of its tile shape). */
 KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
 
-/* Form `shape` (1 .. 6) of the partition passes for `dtype`: *threads CTA threads, each
- * holding *keys_per_thread keys (a multiple of the 128-bit vector). Forms 1-3 load a
- * tile straight into registers. Forms 4-6 (*staged = 1) have the same shapes as 1-3,
- * but stage the next tile into shared memory by a bulk copy while the current one is
- * finished. */
+/* Form `shape` (1 .. 9) of the partition passes for `dtype`: CTAs of *threads threads,
+ * whose tile-holding threads each hold *keys_per_thread keys (a multiple of the 128-bit
+ * vector). Three CTA shapes come in three kinds (*form):
+ *   0 (shapes 1-3): every thread loads its keys of a tile straight into registers;
+ *   1 (shapes 4-6): the next tile is staged into shared memory by a bulk copy while the
+ *                   current one is finished;
+ *   2 (shapes 7-9): warp roles, with one warp loading tiles by bulk copies, one warp
+ *                   running look-backs and completions, and the rest (threads - 64)
+ *                   counting, scattering and writing, so consecutive tiles overlap. */
 KSORT_API ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
-                                          int32_t *keys_per_thread, int32_t *staged);
+                                          int32_t *keys_per_thread, int32_t *form);
 
 /* Failure-path check: runs one device-side wait, of the kind the partition's look-back
  * uses, on a flag that nothing ever sets. The wait gives up after limit_ms (1..60000),

@@ -221,12 +221,13 @@ def ksort_get_tuning(dtype: int) -> dict:
             "tile_shape": t.tile_shape}
 
 
-def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, bool]:
-    """(threads, keys per thread, staged) of partition-pass form `shape` (1-based)."""
-    nt, ipt, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
+    """(threads, keys per tile-holding thread, form) of partition-pass form `shape`
+    (1-based); form 0 registers, 1 staged, 2 warp roles."""
+    nt, ipt, fm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().ksort_tile_shape(dtype, shape, ctypes.byref(nt), ctypes.byref(ipt),
-                                   ctypes.byref(st)), "ksort_tile_shape")
-    return int(nt.value), int(ipt.value), bool(st.value)
+                                   ctypes.byref(fm)), "ksort_tile_shape")
+    return int(nt.value), int(ipt.value), int(fm.value)
 
 
 def ksort_max_cutoff(dtype: int) -> int:

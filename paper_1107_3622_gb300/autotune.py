@@ -1,6 +1,7 @@
-"""Autotuner of libksort: picks, for one key type and workload, the tile shape of the
-partition passes (threads x keys per thread), the shared-memory cutoff below which
-sub-arrays are finished in SMEM, and the finisher's CTAs per SM.
+"""Autotuner of libksort: picks, for one key type and workload (a sort, a batch of sorts
+or a single partition), the form of the partition passes (kernel kind and threads x
+keys per thread), the shared-memory cutoff below which sub-arrays are finished in SMEM,
+and the finisher's CTAs per SM.
 
 Every candidate runs the real workload through the C ABI on the current device. The
 input is restored from a pristine copy and L2 flushed before each timed run, and CUDA
@@ -22,12 +23,12 @@ import threading
 import numpy as np
 
 from . import F32, F64, U32, _HERE, ksort_get_device_error, ksort_get_tuning, \
-    ksort_max_cutoff, ksort_reserve_workspace, ksort_set_tuning, ksort_sort, \
-    ksort_sort_batched
+    ksort_max_cutoff, ksort_partition_out, ksort_reserve_workspace, ksort_set_tuning, \
+    ksort_sort, ksort_sort_batched
 
 _NAMES = {F32: "f32", F64: "f64", U32: "u32"}
 CUTOFFS = (1024, 2048, 4096, 8192, 16384)
-SHAPES = (1, 2, 3, 4, 5, 6)
+SHAPES = tuple(range(1, 10))
 FINISHER_CTAS = (-1, 3, 2)
 _L2_FLUSH_BYTES = 256 << 20
 _lock = threading.Lock()
@@ -55,9 +56,9 @@ def device_key() -> str:
 
 
 def workload_key(kind: str, dtype: int, n: int = 0, lengths=None) -> str:
-    """Sorts are bucketed by log2 n; batches by array count and total keys."""
-    if kind == "sort":
-        return f"sort:{_NAMES[dtype]}:2^{round(math.log2(max(n, 2)))}"
+    """Sorts and partitions are bucketed by log2 n; batches by array count and keys."""
+    if kind in ("sort", "partition"):
+        return f"{kind}:{_NAMES[dtype]}:2^{round(math.log2(max(n, 2)))}"
     lengths = np.asarray(lengths)
     total = int(lengths.sum())
     return (f"batched:{_NAMES[dtype]}:{len(lengths)}x"
@@ -107,7 +108,7 @@ class _Runner:
         import ksort_inputs as gen
         self.kind, self.dtype = kind, dtype
         name = _NAMES[dtype]
-        if kind == "sort":
+        if kind in ("sort", "partition"):
             self.total, self.offsets, self.arrays = n, None, 1
         else:
             off = gen.offsets_from_lengths(np.asarray(lengths, np.int64))
@@ -115,10 +116,13 @@ class _Runner:
             self.offsets = torch.from_numpy(off).cuda()
         self.pristine = gen.uniform_torch(name, seed, self.total, device="cuda")
         self.keys = torch.empty_like(self.pristine)
+        self.index = torch.zeros(1, dtype=torch.int64, device="cuda")
         self.flush = torch.empty(_L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def call(self):
-        if self.kind == "sort":
+        if self.kind == "partition":  # out of place: the input stays pristine
+            ksort_partition_out(self.dtype, self.pristine, self.keys, self.total, self.index)
+        elif self.kind == "sort":
             ksort_sort(self.dtype, self.keys, self.total)
         else:
             ksort_sort_batched(self.dtype, self.keys, self.offsets, self.arrays, self.total)
@@ -150,6 +154,12 @@ class _Runner:
         self.call()
         k = self.keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF \
             if self.dtype == U32 else self.keys
+        if self.kind == "partition":
+            i = int(self.index.item())
+            src = self.pristine.view(torch.int32).to(torch.int64) & 0xFFFFFFFF \
+                if self.dtype == U32 else self.pristine
+            return bool(k[i] == src[0]) and bool((k[:i] < k[i]).all()) and \
+                bool((k[i + 1:] >= k[i]).all())
         if self.kind == "sort":
             return bool((k[1:] >= k[:-1]).all())
         off = self.offsets
@@ -165,8 +175,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
              seed: int | None = None, use_cache: bool = True, max_rounds: int = 2) -> dict:
     """Searches and applies the best tuning for one workload; returns the cache entry."""
     import ksort_inputs as gen
-    if kind not in ("sort", "batched"):
-        raise ValueError("kind is 'sort' or 'batched'")
+    if kind not in ("sort", "batched", "partition"):
+        raise ValueError("kind is 'sort', 'partition' or 'batched'")
     if use_cache:
         e = apply_cached(kind, dtype, n, lengths)
         if e is not None:
@@ -191,6 +201,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 
     best_ms = measure(best)
     axes = (("tile_shape", SHAPES), ("cutoff", cutoffs), ("ctas_per_sm", FINISHER_CTAS))
+    if kind == "partition":  # a single partition runs tile passes only
+        axes = axes[:1]
     for _ in range(max_rounds):
         improved = False
         for name, values in axes:

@@ -592,14 +592,14 @@ int32_t ksort_tile_keys(ksort_dtype_t dtype) {
 }
 
 ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
-                                int32_t *keys_per_thread, int32_t *staged) {
+                                int32_t *keys_per_thread, int32_t *form) {
   if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
-  if (shape < 1 || shape > kTileVariants || !threads || !keys_per_thread || !staged)
+  if (shape < 1 || shape > kTileVariants || !threads || !keys_per_thread || !form)
     return KSORT_ERR_INVALID_ARG;
   const KernelInfo ki = ops(dtype).info(shape - 1);
   *threads = ki.block;
   *keys_per_thread = ki.keys_per_thread;
-  *staged = ki.staged;
+  *form = ki.form;
   return KSORT_OK;
 }
 

@@ -1063,6 +1063,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Waits for phase `parity` of `bar` to complete; false if limit_ns passed first.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
                                           unsigned long long limit_ns) {
@@ -1082,8 +1093,11 @@ struct PipeTile {
   unsigned long long k;     // ticket
   unsigned t;               // tile index within the item
   int vlo, vhi;             // classified keys of the tile: [vlo, vhi)
-  int agg;                  // aggregate already published
+  int agg;                  // its aggregate is published already
 };
+
+// Ticket states of the staged kernel: none, claimed (not yet issued), copy in flight.
+enum : int { kPipeNone = 0, kPipeClaimed = 1, kPipeCopying = 2 };
 
 template <int NW>
 struct PipeCtaShared {
@@ -1091,13 +1105,13 @@ struct PipeCtaShared {
   unsigned long long E;
   int abort;
   int last;
-  int r;          // status of the ticket the CTA waited for
-  int next;       // next tile: 1 claimed but not yet issued, 2 issued and being copied
-  int fail;       // the early count gave up waiting for the next tile's keys
-  unsigned early_L;
-  long long ch;   // item whose record is cached in `ci`
+  int r;            // status of the ticket the CTA waited for
+  int cs, ns, nns;  // states of the current, next and next-but-one tiles
+  int fail;         // a warp found the next tile's keys not landed yet
+  unsigned early_L; // less keys of the next tile, counted early
+  long long ch;     // item whose record is cached in `ci`
   Item ci;
-  PipeTile cur, nxt;
+  PipeTile cur, nxt, nn;
   unsigned long long cidx[2], ct0[2];
   unsigned ctiles[2];
   unsigned long long bar[2];
@@ -1130,37 +1144,59 @@ __device__ __forceinline__ void pipe_issue(const SortParams &p, const PipeTile &
   constexpr int VEC = Vec<K>::N;
   const K *src = static_cast<const K *>((pt.it.flags & kItemScratch) ? p.scratch : p.keys);
   const unsigned bytes = (unsigned)((pt.vhi + VEC - 1) / VEC * VEC) * (unsigned)sizeof(K);
-  fence_proxy_async();  // earlier generic writes of the keys before the async-proxy read
+  fence_proxy_async();  // earlier generic accesses before the async-proxy copy
   mbar_expect_tx(bar, bytes);
   bulk_g2s(sdst, src + pt.lo, bytes, bar);
+}
+
+// Thread 0: if ticket k is issued (one acquire load of its ticket-map entry), fill `pt`
+// and start the copy of its keys into `sdst`; returns the ticket's new state.
+template <typename K, int TILE>
+__device__ __forceinline__ int pipe_try_start(const SortParams &p, unsigned epoch,
+                                              unsigned long long k, unsigned long long v,
+                                              PipeTile &pt, Item *ci, long long *ch, K *sdst,
+                                              unsigned long long *bar) {
+  pt.k = k;
+  if ((unsigned)(v >> 32) != epoch) return kPipeClaimed;
+  pipe_geom<K, TILE>(p, pt, ci, ch, k, (long long)(v & 0xffffffffull));
+  pipe_issue<K>(p, pt, sdst, bar);
+  trace_mark(p, k, 1);  // copy issued
+  return kPipeCopying;
+}
+
+__device__ __forceinline__ unsigned long long tmap_probe(const SortParams &p,
+                                                         unsigned long long k) {
+  return k < p.lb_cap ? ld_acquire(&p.tmap[k]) : 0ull;
 }
 
 template <typename K, int TILE>
 constexpr size_t pipe_smem_bytes() { return (size_t)3 * TILE * sizeof(K); }
 
 // Phase 1, staged form of tile_kernel: the same tile passes, Steps and output, with the
-// next tile overlapped. Right after the current tile's keys arrive, thread 0 claims the
-// next ticket; if that ticket is already issued, its keys start streaming into the
-// second shared-memory buffer by one bulk copy. While warp 0 runs the current tile's
-// look-back, the other warps scatter and then count the next tile in shared memory and
-// publish its aggregate as soon as its keys land, so later tiles' look-backs do not
-// wait for this CTA. A claimed ticket that is not issued yet is waited for only after
-// the current tile is complete (its completion may be what issues it).
-// Dynamic shared memory: two input tiles and the output tile.
+// keys of the next tile already in shared memory when a tile starts. A CTA owns two
+// input buffers. Once a tile's output is written, its buffer is free: another thread
+// then claims the ticket after the next one and, if it is issued, starts one bulk copy of
+// its keys into that buffer, while thread 0 runs the tile's completion atomic (whose
+// release waits for the tile's stores). A copy so has a whole tile period to land. While
+// warp 0 runs a tile's look-back, the other warps count the next tile in shared memory,
+// if its keys have landed, and publish its aggregate, so later tiles' look-backs find it
+// early. A CTA holds at most two tickets beyond the finished one. A claimed ticket that
+// is not issued yet is probed again after the next tile, and waited for only when it is
+// the CTA's current tile and its previous tile is complete (that completion may be what
+// issues it). Dynamic shared memory: two input tiles and the output tile.
 template <typename K, int NT, int IPT>
 __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(SortParams p) {
   constexpr int TILE = NT * IPT;
   constexpr int VEC = Vec<K>::N;
   constexpr int NV = IPT / VEC;
   constexpr int NW = NT / 32;
-  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0 && NW > 1, "bad tile shape");
+  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0, "bad tile shape");
   using V = typename Vec<K>::T;
   extern __shared__ __align__(128) unsigned char pipe_smem[];
   K *const sin0 = reinterpret_cast<K *>(pipe_smem);
   K *const sout = sin0 + 2 * TILE;
   __shared__ PipeCtaShared<NW> sh;
   K *const buf0 = static_cast<K *>(p.keys);
-  K *const buf1 = static_cast<K *>(p.scratch);
   Control *ctl = p.ctl;
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -1173,54 +1209,42 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
     mbar_init(&sh.bar[1], 1);
     fence_mbar_init();
     sh.ch = -1;
-    sh.next = 0;
-    const unsigned long long k = atomicAdd(&ctl->tq_head, 1ull);
-    trace_mark(p, k, 0);  // claimed
-    long long h = 0;
-    const int r = wait_ticket(p, epoch, k, &h);
-    sh.r = r;
-    if (r > 0) {
-      pipe_geom<K, TILE>(p, sh.cur, &sh.ci, &sh.ch, k, h);
-      pipe_issue<K>(p, sh.cur, sin0, &sh.bar[0]);
-      trace_mark(p, k, 1);  // copy issued
-    }
+    sh.cur.k = atomicAdd(&ctl->tq_head, 1ull);
+    trace_mark(p, sh.cur.k, 0);  // claimed
+    sh.cs = kPipeClaimed;
+    sh.ns = sh.nns = kPipeNone;
+    sh.fail = 0;
+    sh.early_L = 0;
   }
   __syncthreads();
-  if (sh.r <= 0) return;
 
   while (true) {
-    // ---- the current tile's keys (copy issued earlier into buffer b)
-    const bool landed = mbar_wait(&sh.bar[b], (phase >> b) & 1u, p.spin_limit_ns);
-    phase ^= 1u << b;
-    K *const sin = sin0 + b * TILE;
-    K *const snx = sin0 + (b ^ 1) * TILE;
-
-    // ---- thread 0: claim the next ticket; start its copy if it is issued already
-    if (tid == 0) {
-      sh.early_L = 0;
-      sh.fail = 0;
-      const unsigned long long kn = atomicAdd(&ctl->tq_head, 1ull);
-      trace_mark(p, kn, 0);  // claimed
-      sh.nxt.k = kn;
-      int state = 1;
-      if (kn < p.lb_cap) {
-        const unsigned long long v = ld_acquire(&p.tmap[kn]);
-        if ((unsigned)(v >> 32) == epoch) {
-          pipe_geom<K, TILE>(p, sh.nxt, &sh.ci, &sh.ch, kn, (long long)(v & 0xffffffffull));
-          pipe_issue<K>(p, sh.nxt, snx, &sh.bar[b ^ 1]);
-          trace_mark(p, kn, 1);  // copy issued
-          state = 2;
+    // ---- a current tile whose ticket was not issued when claimed: wait for it now
+    if (sh.cs == kPipeClaimed) {
+      if (tid == 0) {
+        long long h = 0;
+        const int r = wait_ticket(p, epoch, sh.cur.k, &h);
+        sh.r = r;
+        if (r > 0) {
+          pipe_geom<K, TILE>(p, sh.cur, &sh.ci, &sh.ch, sh.cur.k, h);
+          pipe_issue<K>(p, sh.cur, sin0 + b * TILE, &sh.bar[b]);
+          trace_mark(p, sh.cur.k, 1);
         }
       }
-      sh.next = state;
+      __syncthreads();
+      if (sh.r <= 0) break;  // phase 1 is over (or aborted); no copy is in flight
     }
+    K *const sin = sin0 + b * TILE;
+    K *const snx = sin0 + (b ^ 1) * TILE;
+    const bool landed = mbar_wait(&sh.bar[b], (phase >> b) & 1u, p.spin_limit_ns);
+    phase ^= 1u << b;
 
     const int vlo = sh.cur.vlo, vhi = sh.cur.vhi;
     const unsigned t = sh.cur.t;
     const Item it = sh.cur.it;
     const long long lo = sh.cur.lo, h = sh.cur.h;
     const unsigned par = it.flags & kItemScratch;
-    K *dst = par ? buf0 : buf1;
+    K *dst = par ? buf0 : static_cast<K *>(p.scratch);
     const K key = bits_key<K>(it.key);  // Step 1: the first element is the key
 
     // ---- count (Step 3) from shared memory
@@ -1261,7 +1285,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
       // the copy did not land in time: record it, let it finish (bounded), stop
       if (tid == 0) raise_error(ctl, kDevTimeout, 0x800000000ull | t);
       mbar_wait(&sh.bar[b], ((phase >> b) & 1u) ^ 1u, p.spin_limit_ns);
-      if (sh.next == 2) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+      if (sh.ns == kPipeCopying) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
       break;
     }
     unsigned L = 0, G = 0, wlx = 0, wgx = 0;
@@ -1276,12 +1300,13 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
       G += c;
     }
     unsigned long long *lb = p.lb + it.lb;
+    const int ns0 = sh.ns;  // state of the next tile for the rest of this iteration
     if (tid == 0) {
-      if (!sh.cur.agg) st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));
+      if (!sh.cur.agg) st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));  // aggregate
       trace_mark(p, sh.cur.k, 2);
     }
 
-    // ---- look-back (warp 0); scatter (all); early count of the next tile (warps 1..)
+    // ---- look-back (warp 0); scatter (everyone); early count of the next tile
     if (w == 0) {
       unsigned long long E = 0;
       int status = 0;
@@ -1310,8 +1335,10 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
         else if ((gebits >> j) & 1u) sout[rg++] = x[j];
       }
     }
-    if (w > 0 && sh.next == 2) {
-      const bool ok = mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+    if (w > 0 && ns0 == kPipeCopying) {
+      // the next tile's copy was started a tile period ago: count it if it has landed
+      // sh.fail and sh.early_L were cleared before the CTA barrier that ended the last tile
+      const bool ok = mbar_test(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
       if (__all_sync(kFull, ok)) {
         const int nlo = sh.nxt.vlo, nhi = sh.nxt.vhi;
         const K nkey = bits_key<K>(sh.nxt.it.key);
@@ -1344,27 +1371,26 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
     }
     __syncthreads();
     const unsigned long long E = sh.E;
-    if (sh.abort) {
-      if (sh.next == 2) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+    long long lbase = 0, gbase = 0;
+    const bool dest_ok = tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase);
+    if (sh.abort || !dest_ok) {
+      if (tid == 0 && !dest_ok && !sh.abort) raise_error(ctl, kDevInternal, 0x500000000ull | t);
+      if (sh.ns == kPipeCopying) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
       break;
     }
 
     // ---- write
-    long long lbase = 0, gbase = 0;
-    if (!tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase)) {
-      if (tid == 0) raise_error(ctl, kDevInternal, 0x500000000ull | t);
-      if (sh.next == 2) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
-      break;
-    }
     copy_out<K, NT>(sout, dst + lbase, L);
     copy_out<K, NT>(sout + L, dst + gbase, G);
     __syncthreads();
 
-    // ---- completion: the last tile of the item places the key and queues both sides
+    // ---- completion (thread 0), and the next copies into the buffers no longer needed
     if (tid == 0) {
       trace_mark(p, sh.cur.k, 4);
       ++st_tiles;
       if (t == it.tiles - 1) atomicExch(&p.ictl[h].less, E + L);
+      // release: this tile's writes (ordered before by the barrier) and `less` become
+      // visible to whichever CTA observes the count reaching tiles
       const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);
       sh.last = done_before == it.tiles - 1;
       sh.ctiles[0] = sh.ctiles[1] = 0;
@@ -1375,7 +1401,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
         if (kpos >= it.end) {
           raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)h);
         } else if (it.flags & kItemPartitionOnly) {
-          dst[kpos] = key;
+          dst[kpos] = key;  // a single partition: the key index is the result
           if (p.key_index) *p.key_index = (long long)c;
         } else {
           buf0[kpos] = key;  // Step 4
@@ -1397,6 +1423,29 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
           }
         }
       }
+      if (ns0 != kPipeCopying) {
+        // the next tile is not in flight: start it (a new claim, or the one claimed
+        // earlier), and if it starts, the one after it into this tile's buffer
+        const unsigned long long kx =
+            ns0 == kPipeClaimed ? sh.nxt.k : atomicAdd(&ctl->tq_head, 1ull);
+        if (ns0 != kPipeClaimed) trace_mark(p, kx, 0);
+        const int st = pipe_try_start<K, TILE>(p, epoch, kx, tmap_probe(p, kx), sh.nxt, &sh.ci,
+                                               &sh.ch, snx, &sh.bar[b ^ 1]);
+        sh.ns = st;
+        sh.nns = kPipeNone;
+        if (st == kPipeCopying) {
+          const unsigned long long kn = atomicAdd(&ctl->tq_head, 1ull);
+          trace_mark(p, kn, 0);
+          sh.nns = pipe_try_start<K, TILE>(p, epoch, kn, tmap_probe(p, kn), sh.nn, &sh.ci,
+                                           &sh.ch, sin, &sh.bar[b]);
+        }
+      }
+    } else if (tid == 32 && ns0 == kPipeCopying) {
+      // the next tile is in flight: the one after it goes into this tile's buffer
+      const unsigned long long kn = atomicAdd(&ctl->tq_head, 1ull);
+      trace_mark(p, kn, 0);
+      sh.nns = pipe_try_start<K, TILE>(p, epoch, kn, tmap_probe(p, kn), sh.nn, &sh.ci, &sh.ch,
+                                       sin, &sh.bar[b]);
     }
     __syncthreads();
     if (sh.last) {
@@ -1404,35 +1453,31 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
       for (int s = 0; s < 2; ++s)
         if (sh.ctiles[s]) publish_tickets(p, epoch, sh.cidx[s], sh.ct0[s], sh.ctiles[s], tid, NT);
       __syncthreads();
-      if (tid == 0) {
+    }
+    if (tid == 0) {
+      if (sh.last) {
         ++st_large;
         st_large_keys += (unsigned long long)(it.end - it.begin);
         __threadfence();
         atomicAdd(&ctl->large_completed, 1ull);
       }
-    }
-
-    // ---- advance: the next tile becomes current (waiting for its ticket if needed)
-    if (tid == 0) {
-      trace_mark(p, sh.cur.k, 6);
+      trace_mark(p, sh.cur.k, 6);  // completed
       if (p.trace && sh.cur.k < (unsigned long long)p.trace_cap)
         p.trace[sh.cur.k * kTraceWords + 7] = blockIdx.x;
-      if (sh.next == 2) {
-        sh.cur = sh.nxt;
-        sh.r = 1;
+      // advance: the next tile becomes current
+      sh.cur = sh.nxt;
+      sh.cs = sh.ns;
+      if (sh.ns == kPipeCopying) {
+        sh.nxt = sh.nn;
+        sh.ns = sh.nns;
       } else {
-        long long hn = 0;
-        const int r = wait_ticket(p, epoch, sh.nxt.k, &hn);
-        sh.r = r;
-        if (r > 0) {
-          pipe_geom<K, TILE>(p, sh.cur, &sh.ci, &sh.ch, sh.nxt.k, hn);
-          pipe_issue<K>(p, sh.cur, snx, &sh.bar[b ^ 1]);
-          trace_mark(p, sh.nxt.k, 1);  // copy issued
-        }
+        sh.ns = kPipeNone;
       }
+      sh.nns = kPipeNone;
+      sh.fail = 0;
+      sh.early_L = 0;
     }
     __syncthreads();
-    if (sh.r <= 0) break;
     b ^= 1;
   }
   if (tid == 0) {
@@ -1440,6 +1485,486 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
     if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
     if (st_large) atomicAdd(&ctl->large_items, st_large);
     if (st_large_keys) atomicAdd(&ctl->large_keys, st_large_keys);
+  }
+}
+
+// ----------------------------------------------------------------------------- warp roles
+// Named barriers (0 is __syncthreads): bar.arrive / bar.sync between warp groups.
+__device__ __forceinline__ void nbar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// bar.sync with an OR over the participants' predicates (the same result in all of them).
+__device__ __forceinline__ bool nbar_or(int id, int count, bool pred) {
+  unsigned out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(out)
+      : "r"((unsigned)pred), "r"(id), "r"(count)
+      : "memory");
+  return out != 0;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Waits for phase `parity` of `bar`; gives up (false) after limit_ns or once the sort is
+// aborted.
+__device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsigned parity,
+                                                   unsigned long long limit_ns,
+                                                   const unsigned *abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (unsigned i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 31u) == 0u) {
+      if (globaltimer() - t0 > limit_ns) return false;
+      if (ld_relaxed(abort_flag) != 0u) return false;
+    }
+  }
+}
+
+// copy_out for a group of NG threads (rank r) instead of the whole CTA.
+template <typename K, int NG>
+__device__ __forceinline__ void copy_out_group(const K *sm, K *g, unsigned count, int r) {
+  constexpr int VEC = Vec<K>::N;
+  using V = typename Vec<K>::T;
+  unsigned head = (unsigned)(((16u - (reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) / sizeof(K));
+  if (head > count) head = count;
+  if (r < (int)head) g[r] = sm[r];
+  const unsigned nvec = (count - head) / VEC;
+  V *gv = reinterpret_cast<V *>(g + head);
+  for (unsigned v = r; v < nvec; v += NG) {
+    K x[VEC];
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) x[l] = sm[head + v * VEC + l];
+    V q;
+    if constexpr (VEC == 4) {
+      q.x = x[0]; q.y = x[1]; q.z = x[2]; q.w = x[3];
+    } else {
+      q.x = x[0]; q.y = x[1];
+    }
+    gv[v] = q;
+  }
+  for (unsigned k = head + nvec * VEC + r; k < count; k += NG) g[k] = sm[k];
+}
+
+// A tile staged in one input buffer (written by the load warp before its copy starts).
+struct WsTile {
+  Item it;
+  long long h, lo;
+  unsigned long long k;
+  unsigned t;
+  int vlo, vhi;
+  int end;  // 1: no more tiles, 2: aborted
+};
+
+// What the look-back warp needs of a counted tile (written by the first data thread).
+struct WsCur {
+  Item it;
+  long long h, lo;
+  unsigned long long k;
+  unsigned t;
+  unsigned L, G;
+  int stop;
+  int agg;  // the data warps published the aggregate already (early count)
+};
+
+// Records that two consecutive tiles use at once are indexed by tile parity.
+template <int ND>
+struct WsShared {
+  unsigned wl[ND], wg[ND];
+  WsCur cur[2];
+  unsigned long long E[2];
+  int abort[2];
+  WsTile rec[2];
+  unsigned long long full[2], empty[2];
+  unsigned long long cidx[2], ct0[2];
+  unsigned ctiles[2];
+  long long ch;  // item cached in `ci` (load warp)
+  Item ci;
+};
+
+// Named barriers; the count and prefix barriers come in two copies, one per tile parity.
+constexpr int kWsBarStart = 1, kWsBarData = 2, kWsBarCnt = 3 /* and 4 */, kWsBarE = 5 /* and 6 */,
+              kWsBarWritten = 7;
+
+template <typename K, int TILE>
+constexpr size_t ws_smem_bytes() { return (size_t)3 * TILE * sizeof(K); }
+
+// Phase 1, warp-specialised form of tile_kernel: the same tile passes, Steps and
+// output, by three groups of warps of one CTA that wait on each other only through
+// named barriers and mbarriers:
+//   warp 1 (load)      claims tickets in order, waits until each is issued, and starts
+//                      one bulk copy of the tile's keys into the input buffer the data
+//                      warps last released (two buffers, full/empty mbarriers). It may
+//                      block on a ticket that is not issued yet without stopping the
+//                      other warps, which finish the tiles already loaded.
+//   warps 2.. (data)   count a tile in shared memory (Step 3), publish its totals,
+//                      scatter it into the output tile, and, once the look-back warp has
+//                      its prefix, write both sides out. While the look-back runs they
+//                      count the next tile early, if its keys have landed, and publish its
+//                      aggregate, so that later tiles' look-backs find it sooner.
+//   warp 0 (look-back) publishes each tile's aggregate and runs its look-back; once the
+//                      data warps have written the tile it runs the completion atomic
+//                      (whose release waits for the tile's stores): the last tile of an
+//                      item places the key (Step 4) and queues both sides (Steps 5-6).
+// The completion of tile i (warp 0) overlaps the loading and counting of tile i+1
+// (data warps). Dynamic shared memory: two input tiles and the output tile.
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_ws_kernel(SortParams p) {
+  constexpr int ND = NT / 32 - 2;  // data warps
+  constexpr int NTD = ND * 32;     // data threads
+  constexpr int TILE = NTD * IPT;
+  constexpr int VEC = Vec<K>::N;
+  constexpr int NV = IPT / VEC;
+  static_assert(IPT % VEC == 0 && IPT <= 32 && ND >= 2, "bad tile shape");
+  using V = typename Vec<K>::T;
+  extern __shared__ __align__(128) unsigned char ws_smem[];
+  K *const sin0 = reinterpret_cast<K *>(ws_smem);  // input tiles 0, 1
+  K *const sout0 = sin0 + 2 * TILE;                // output tile
+  __shared__ WsShared<ND> sh;
+  K *const buf0 = static_cast<K *>(p.keys);
+  Control *ctl = p.ctl;
+  const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+
+  if (tid == 0) {
+    mbar_init(&sh.full[0], 1);
+    mbar_init(&sh.full[1], 1);
+    mbar_init(&sh.empty[0], ND);
+    mbar_init(&sh.empty[1], ND);
+    fence_mbar_init();
+    sh.ch = -1;
+  }
+  __syncthreads();  // the only CTA-wide barrier
+
+  if (w == 1) {
+    // ------------------------------------------------------------------ load warp
+    unsigned eph = 0;       // bit j: parity of the next release of buffer j
+    int fills[2] = {0, 0};  // copies started into buffer j
+    int j = 0;
+    while (true) {
+      if (fills[j] > 0) {
+        // the data warps release buffer j once they hold its keys in registers
+        const bool ok = mbar_wait_or_abort(&sh.empty[j], (eph >> j) & 1u, p.spin_limit_ns,
+                                           &ctl->abort);
+        eph ^= 1u << j;
+        if (!ok) break;  // the consumers stopped (abort or an error elsewhere)
+      }
+      int stop = 0;
+      if (lane == 0) {
+        const unsigned long long k = atomicAdd(&ctl->tq_head, 1ull);
+        trace_mark(p, k, 0);  // claimed
+        long long h = 0;
+        const int r = wait_ticket(p, epoch, k, &h);
+        WsTile &rc = sh.rec[j];
+        if (r > 0) {
+          if (h != sh.ch) {
+            load_item(p.items + h, &sh.ci);
+            sh.ch = h;
+          }
+          rc.it = sh.ci;
+          const K *src = static_cast<const K *>((rc.it.flags & kItemScratch) ? p.scratch : p.keys);
+          rc.k = k;
+          rc.h = h;
+          rc.t = (unsigned)(k - rc.it.lb);
+          rc.lo = tile_base(src, rc.it.begin) + (long long)rc.t * TILE;
+          const long long first = rc.it.begin + 1;
+          rc.vlo = (int)(first > rc.lo ? first - rc.lo : 0);
+          rc.vhi = (int)(rc.it.end - rc.lo < TILE ? rc.it.end - rc.lo : TILE);
+          rc.end = 0;
+          // whole 16-byte blocks that hold classified keys: inside the buffer's allocation
+          const unsigned bytes = (unsigned)((rc.vhi + VEC - 1) / VEC * VEC) * (unsigned)sizeof(K);
+          fence_proxy_async();  // earlier generic accesses before the async-proxy copy
+          mbar_expect_tx(&sh.full[j], bytes);
+          bulk_g2s(sin0 + j * TILE, src + rc.lo, bytes, &sh.full[j]);
+          trace_mark(p, k, 1);  // copy issued
+        } else {
+          rc.end = r == 0 ? 1 : 2;
+          mbar_expect_tx(&sh.full[j], 0u);  // completes the phase without a copy
+          stop = 1;
+        }
+      }
+      stop = __shfl_sync(kFull, stop, 0);
+      ++fills[j];
+      if (stop) break;
+      j ^= 1;
+    }
+    // a copy still in flight lands before the CTA may leave (bounded)
+    if (lane == 0) {
+      for (int q = 0; q < 2; ++q)
+        if (fills[q] > 0) mbar_wait(&sh.full[q], (unsigned)(fills[q] - 1) & 1u, p.spin_limit_ns);
+    }
+    return;
+  }
+
+  if (w == 0) {
+    // ------------------------------------------------------------------ look-back warp
+    unsigned long long st_tiles = 0, st_lb = 0, st_large = 0, st_large_keys = 0;
+    int par = 0;  // parity of the current tile
+    while (true) {
+      if (par) nbar_sync(kWsBarCnt + 1, NTD + 32);  // the data warps counted the tile
+      else nbar_sync(kWsBarCnt, NTD + 32);
+      const WsCur c = sh.cur[par];
+      if (c.stop) break;
+      unsigned long long *lb = p.lb + c.it.lb;
+      if (lane == 0) {
+        if (!c.agg) st_relaxed(&lb[c.t], lb_pack(epoch, c.t == 0, c.L));  // aggregate
+        trace_mark(p, c.k, 2);
+      }
+      unsigned long long E = 0;
+      int status = 0;
+      if (c.t > 0) {
+        unsigned long long steps = 0;
+        status = lookback(lb, c.t, epoch, p.spin_limit_ns, &ctl->abort, &E, &steps);
+        if (lane == 0) {
+          if (status == 0) st_relaxed(&lb[c.t], lb_pack(epoch, true, (unsigned)(E + c.L)));
+          st_lb += steps;
+        }
+      }
+      if (lane == 0) {
+        if (status == 1) raise_error(ctl, kDevTimeout, 0x100000000ull | c.t);
+        sh.E[par] = E;
+        sh.abort[par] = status == 0 ? 0 : 1;
+        trace_mark(p, c.k, 3);
+      }
+      if (par) nbar_arrive(kWsBarE + 1, NTD + 32);
+      else nbar_arrive(kWsBarE, NTD + 32);
+      if (status != 0) break;  // the data warps see the abort and stop too
+      nbar_sync(kWsBarWritten, NTD + 32);  // the data warps wrote the tile
+      const unsigned cpar = c.it.flags & kItemScratch;
+      K *dst = cpar ? buf0 : static_cast<K *>(p.scratch);
+      int last = 0;
+      if (lane == 0) {
+        trace_mark(p, c.k, 4);
+        ++st_tiles;
+        if (c.t == c.it.tiles - 1) atomicExch(&p.ictl[c.h].less, E + c.L);
+        // release: the tile's writes (ordered before by the named barrier) and `less`
+        // become visible to whichever CTA observes the count reaching tiles
+        const unsigned done_before = atom_add_release(&p.ictl[c.h].done, 1u);
+        last = done_before == c.it.tiles - 1;
+        sh.ctiles[0] = sh.ctiles[1] = 0;
+        if (last) {
+          __threadfence();
+          const unsigned long long cc = ld_acquire(&p.ictl[c.h].less);
+          const long long kpos = c.it.begin + (long long)cc;
+          const K key = bits_key<K>(c.it.key);
+          if (kpos >= c.it.end) {
+            raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)c.h);
+          } else if (c.it.flags & kItemPartitionOnly) {
+            dst[kpos] = key;  // a single partition: the key index is the result
+            if (p.key_index) *p.key_index = (long long)cc;
+          } else {
+            buf0[kpos] = key;  // Step 4
+            const unsigned cflags = cpar ^ kItemScratch;
+            const long long cb[2] = {c.it.begin, kpos + 1};
+            const long long ce[2] = {kpos, c.it.end};
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {  // Steps 5-6
+              const long long mm = ce[s] - cb[s];
+              if (mm == 1) {
+                if (cflags & kItemScratch) buf0[cb[s]] = __ldcg(dst + cb[s]);
+              } else if (mm >= 2) {
+                unsigned long long t0 = 0;
+                unsigned tiles = 0;
+                sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb[s], ce[s], cflags, &t0, &tiles);
+                sh.ct0[s] = t0;
+                sh.ctiles[s] = tiles;
+              }
+            }
+          }
+        }
+      }
+      last = __shfl_sync(kFull, last, 0);
+      if (last) {
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if (sh.ctiles[s]) publish_tickets(p, epoch, sh.cidx[s], sh.ct0[s], sh.ctiles[s], lane, 32);
+        __syncwarp();
+        if (lane == 0) {
+          ++st_large;
+          st_large_keys += (unsigned long long)(c.it.end - c.it.begin);
+          __threadfence();
+          atomicAdd(&ctl->large_completed, 1ull);
+        }
+      }
+      if (lane == 0) {
+        trace_mark(p, c.k, 6);  // completed
+        if (p.trace && c.k < (unsigned long long)p.trace_cap)
+          p.trace[c.k * kTraceWords + 7] = blockIdx.x;
+      }
+      par ^= 1;
+    }
+    if (lane == 0) {
+      if (st_tiles) atomicAdd(&ctl->tiles, st_tiles);
+      if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
+      if (st_large) atomicAdd(&ctl->large_items, st_large);
+      if (st_large_keys) atomicAdd(&ctl->large_keys, st_large_keys);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------------- data warps
+  const int dt = tid - 64, dw = w - 2;
+  unsigned fph = 0;   // bit j: parity of the next completion of input buffer j
+  int b = 0;          // input buffer of the current tile
+  int par = 0;        // parity of the current tile (its records and barriers)
+  int early = 0;      // the current tile's aggregate was published by an early count
+  while (true) {
+    const bool landed = mbar_wait(&sh.full[b], (fph >> b) & 1u, 4 * p.spin_limit_ns);
+    fph ^= 1u << b;
+    const WsTile rc = sh.rec[b];
+    // the same decision in every data warp: stop on the end of the tiles, an abort or a
+    // copy that never landed
+    if (nbar_or(kWsBarStart, NTD, !landed || rc.end != 0)) {
+      if (dt == 0) {
+        if (!landed) raise_error(ctl, kDevTimeout, 0x800000000ull);
+        sh.cur[par].stop = 1;
+      }
+      if (par) nbar_arrive(kWsBarCnt + 1, NTD + 32);  // lets the look-back warp see the stop
+      else nbar_arrive(kWsBarCnt, NTD + 32);
+      break;
+    }
+    K *const sin = sin0 + b * TILE;
+    const K key = bits_key<K>(rc.it.key);  // Step 1: the first element is the key
+    K x[IPT];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const V q = *reinterpret_cast<const V *>(sin + (v * NTD + dt) * VEC);
+      if constexpr (VEC == 4) {
+        x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
+      } else {
+        x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sh.empty[b]);  // this warp's keys are in registers
+    // ---- count (Step 3)
+    unsigned lessbits = 0, gebits = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        const int jx = v * VEC + l, kk = (v * NTD + dt) * VEC + l;
+        const bool valid = kk >= rc.vlo && kk < rc.vhi;
+        const bool le = goes_left(key, x[jx]);
+        lessbits |= (unsigned)(valid && le) << jx;
+        gebits |= (unsigned)(valid && !le) << jx;
+      }
+    }
+    const unsigned mine = (unsigned)__popc(lessbits) | ((unsigned)__popc(gebits) << 16);
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) {
+      sh.wl[dw] = incl & 0xffffu;
+      sh.wg[dw] = incl >> 16;
+    }
+    nbar_sync(kWsBarData, NTD);
+    unsigned L = 0, G = 0, wlx = 0, wgx = 0;
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+      const unsigned a = sh.wl[i], c = sh.wg[i];
+      if (i < dw) {
+        wlx += a;
+        wgx += c;
+      }
+      L += a;
+      G += c;
+    }
+    if (dt == 0) {
+      WsCur &c = sh.cur[par];
+      c.it = rc.it;
+      c.h = rc.h;
+      c.lo = rc.lo;
+      c.k = rc.k;
+      c.t = rc.t;
+      c.L = L;
+      c.G = G;
+      c.stop = 0;
+      c.agg = early;
+    }
+    if (par) nbar_arrive(kWsBarCnt + 1, NTD + 32);
+    else nbar_arrive(kWsBarCnt, NTD + 32);
+    // ---- scatter into the output tile (its last readers wrote it out before the data
+    // warps reached kWsBarData above)
+    {
+      const unsigned excl = incl - mine;
+      unsigned rl = wlx + (excl & 0xffffu);
+      unsigned rg = L + wgx + (excl >> 16);
+#pragma unroll
+      for (int jx = 0; jx < IPT; ++jx) {
+        if ((lessbits >> jx) & 1u) sout0[rl++] = x[jx];
+        else if ((gebits >> jx) & 1u) sout0[rg++] = x[jx];
+      }
+    }
+    // ---- while the look-back runs: count the next tile early if its keys have landed,
+    // and publish its aggregate, so that later tiles' look-backs find it sooner
+    {
+      const unsigned nb = b ^ 1;
+      const bool have = mbar_test(&sh.full[nb], (fph >> nb) & 1u);
+      early = 0;
+      if (!nbar_or(kWsBarStart, NTD, !have)) {
+        const WsTile &rn = sh.rec[nb];
+        if (rn.end == 0) {
+          const K nkey = bits_key<K>(rn.it.key);
+          const K *snb = sin0 + nb * TILE;
+          unsigned cnt = 0;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const V q = *reinterpret_cast<const V *>(snb + (v * NTD + dt) * VEC);
+            K y[VEC];
+            if constexpr (VEC == 4) {
+              y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
+            } else {
+              y[0] = q.x; y[1] = q.y;
+            }
+#pragma unroll
+            for (int l = 0; l < VEC; ++l) {
+              const int kk = (v * NTD + dt) * VEC + l;
+              cnt += (kk >= rn.vlo && kk < rn.vhi && goes_left(nkey, y[l])) ? 1u : 0u;
+            }
+          }
+          cnt = __reduce_add_sync(kFull, cnt);
+          if (lane == 0) sh.wl[dw] = cnt;  // every data warp read its prefixes above
+          nbar_sync(kWsBarData, NTD);
+          if (dt == 0) {
+            unsigned tot = 0;
+#pragma unroll
+            for (int i = 0; i < ND; ++i) tot += sh.wl[i];
+            st_relaxed(&p.lb[rn.it.lb + rn.t], lb_pack(epoch, rn.t == 0, tot));
+            trace_mark(p, rn.k, 5);  // aggregate published early
+          }
+          early = 1;
+        }
+      }
+    }
+    // ---- the prefix, then write both sides
+    if (par) nbar_sync(kWsBarE + 1, NTD + 32);  // all scatters done, prefix known
+    else nbar_sync(kWsBarE, NTD + 32);
+    if (sh.abort[par]) break;
+    const unsigned long long E = sh.E[par];
+    long long lbase = 0, gbase = 0;
+    K *dst = (rc.it.flags & kItemScratch) ? buf0 : static_cast<K *>(p.scratch);
+    if (!tile_dest(rc.it.begin, rc.it.end, rc.lo, rc.t, E, L, G, &lbase, &gbase)) {
+      // impossible prefixes: record, and write nothing (the other warps decide the same)
+      if (dt == 0) raise_error(ctl, kDevInternal, 0x500000000ull | rc.t);
+    } else {
+      copy_out_group<K, NTD>(sout0, dst + lbase, L, dt);
+      copy_out_group<K, NTD>(sout0 + L, dst + gbase, G, dt);
+    }
+    nbar_arrive(kWsBarWritten, NTD + 32);
+    par ^= 1;
+    b ^= 1;
   }
 }
 

@@ -91,18 +91,19 @@ struct SortParams {
 constexpr int kTraceWords = 8;
 
 // Host-side launch interface, one explicit instantiation per key type. `variant`
-// selects one of kTileVariants compiled forms of the tile passes: three tile shapes
-// (variants 0-2) of tile_kernel, and the same shapes staged through shared memory by
-// bulk copies (variants 3-5, tile_pipe_kernel).
+// selects one of kTileVariants compiled forms of the tile passes, for three CTA shapes
+// each: tile_kernel (variants 0-2, keys loaded into registers), tile_pipe_kernel (3-5,
+// staged through shared memory by bulk copies) and tile_ws_kernel (6-8, warp roles).
 constexpr int kTileShapes = 3;
-constexpr int kTileVariants = 2 * kTileShapes;
+constexpr int kTileForms = 3;
+constexpr int kTileVariants = kTileForms * kTileShapes;
 
 struct KernelInfo {
   int block;          // threads per tile-pass CTA
   int tile_keys;      // keys per tile pass
   int max_cutoff;     // largest shared-memory item the kernels support
   int keys_per_thread;
-  int staged;         // 1: tile_pipe_kernel
+  int form;           // 0 tile_kernel, 1 tile_pipe_kernel, 2 tile_ws_kernel
 };
 
 template <typename K>

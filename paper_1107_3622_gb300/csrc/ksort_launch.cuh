@@ -23,14 +23,18 @@ template <> struct Shapes<double> {
   static constexpr int IPT[kTileShapes] = {8, 4, 8};
 };
 
-// Variant V: shape V % kTileShapes, staged through shared memory when V >= kTileShapes.
+// Variant V: CTA shape V % kTileShapes in form V / kTileShapes (0 registers, 1 staged,
+// 2 warp roles, whose tile is the data warps' share: two warps load and look back).
 template <typename K, int V>
 struct ShapeOf {
+  static constexpr int FORM = V / kTileShapes;
   static constexpr int NT = Shapes<K>::NT[V % kTileShapes];
   static constexpr int IPT = Shapes<K>::IPT[V % kTileShapes];
-  static constexpr int TILE = NT * IPT;
-  static constexpr bool STAGED = V >= kTileShapes;
-  static constexpr size_t SMEM = STAGED ? dev::pipe_smem_bytes<K, TILE>() : 0;
+  static constexpr int TILE = (FORM == 2 ? NT - 64 : NT) * IPT;
+  static constexpr bool STAGED = FORM != 0;
+  static constexpr size_t SMEM = FORM == 2   ? dev::ws_smem_bytes<K, TILE>()
+                                 : STAGED    ? dev::pipe_smem_bytes<K, TILE>()
+                                             : 0;
 };
 
 // Calls f(ShapeOf<K, v>{}) for the run-time variant v (out-of-range values: variant 0).
@@ -42,6 +46,9 @@ decltype(auto) with_shape(int v, F &&f) {
     case 3: return f(ShapeOf<K, 3>{});
     case 4: return f(ShapeOf<K, 4>{});
     case 5: return f(ShapeOf<K, 5>{});
+    case 6: return f(ShapeOf<K, 6>{});
+    case 7: return f(ShapeOf<K, 7>{});
+    case 8: return f(ShapeOf<K, 8>{});
     default: return f(ShapeOf<K, 0>{});
   }
 }
@@ -50,7 +57,8 @@ decltype(auto) with_shape(int v, F &&f) {
 template <typename K, typename S>
 cudaError_t tile_kernel_of(void (**fn)(SortParams)) {
   if constexpr (S::STAGED) {
-    *fn = dev::tile_pipe_kernel<K, S::NT, S::IPT>;
+    if constexpr (S::FORM == 2) *fn = dev::tile_ws_kernel<K, S::NT, S::IPT>;
+    else *fn = dev::tile_pipe_kernel<K, S::NT, S::IPT>;
     cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::SMEM);
     if (e != cudaSuccess) return e;
@@ -73,7 +81,7 @@ template <typename K>
 KernelInfo Launcher<K>::info(int variant) {
   return with_shape<K>(variant, [](auto s) {
     using S = decltype(s);
-    return KernelInfo{S::NT, S::TILE, max_cutoff<K>(), S::IPT, S::STAGED ? 1 : 0};
+    return KernelInfo{S::NT, S::TILE, max_cutoff<K>(), S::IPT, S::FORM};
   });
 }
 

@@ -93,21 +93,22 @@ def test_oracle_and_library_share_no_code():
 def test_tile_shapes_and_tuning_fields(lib):
     import paper_1107_3622_gb300 as ks
     for code in (ks.F32, ks.F64, ks.U32):
-        shapes = [ks.ksort_tile_shape(code, s) for s in range(1, 7)]
+        shapes = [ks.ksort_tile_shape(code, s) for s in range(1, 10)]
         vec = 2 if code == ks.F64 else 4
         for nt, ipt, _ in shapes:
             assert nt % 32 == 0 and ipt % vec == 0 and ipt <= 32
-        assert len(set(shapes)) == 6
-        assert [st for _, _, st in shapes] == [False] * 3 + [True] * 3
-        assert [s[:2] for s in shapes[:3]] == [s[:2] for s in shapes[3:]]
+        assert len(set(shapes)) == 9
+        assert [fm for _, _, fm in shapes] == [0] * 3 + [1] * 3 + [2] * 3
+        assert [s[:2] for s in shapes[:3]] == [s[:2] for s in shapes[3:6]] == \
+            [s[:2] for s in shapes[6:]]
         with pytest.raises(ks.KSortError):
             ks.ksort_tile_shape(code, 0)
         with pytest.raises(ks.KSortError):
-            ks.ksort_tile_shape(code, 7)
+            ks.ksort_tile_shape(code, 10)
         before = ks.ksort_get_tuning(code)
-        assert before["tile_shape"] in range(1, 7)
+        assert before["tile_shape"] in range(1, 10)
         with pytest.raises(ks.KSortError):
-            ks.ksort_set_tuning(code, tile_shape=7)
+            ks.ksort_set_tuning(code, tile_shape=10)
         with pytest.raises(ks.KSortError):
             ks.ksort_set_tuning(code, ctas_per_sm=-2)
         ks.ksort_set_tuning(code, tile_shape=2)

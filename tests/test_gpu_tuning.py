@@ -44,15 +44,15 @@ def _oracle(ref, a):
     return b
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", list(range(1, 10)))
 @pytest.mark.parametrize("dtype", list(DTYPES))
 def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
     import torch
     code = DTYPES[dtype]
     ks.ksort_set_tuning(code, tile_shape=shape)
-    nt, ipt, _ = ks.ksort_tile_shape(code, shape)
-    assert ks.ksort_tile_keys(code) == nt * ipt
-    tile = nt * ipt
+    nt, ipt, form = ks.ksort_tile_shape(code, shape)
+    tile = (nt - 64 if form == 2 else nt) * ipt
+    assert ks.ksort_tile_keys(code) == tile
     for n in (tile - 1, tile + 1, 3 * tile + 5, 250_003):
         a = gen.make("uniform", dtype, n, gen.seed_for(6, shape, n % 1009))
         assert _sort(ks, a).tobytes() == _oracle(ref, a).tobytes()
@@ -66,7 +66,7 @@ def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
         assert np.sort(got[i + 1:]).tobytes() == np.sort(b[ri + 1:]).tobytes()
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", list(range(1, 10)))
 def test_tile_shapes_batched(ref, ks, restore, shape):
     import torch
     ks.ksort_set_tuning(0, tile_shape=shape)
@@ -101,7 +101,8 @@ def test_autotuner_searches_applies_and_caches(ks, restore, tmp_path, monkeypatc
     assert t["tile_shape"] == e["tuning"]["tile_shape"]
     assert t["cutoff"] == e["tuning"]["cutoff"]
     assert len(e["candidates"]) >= len(autotune.SHAPES)
-    assert min(c["ms"] for c in e["candidates"]) == pytest.approx(e["ms"])
+    # a candidate replaces the incumbent only when at least 0.5 % faster
+    assert e["ms"] <= min(c["ms"] for c in e["candidates"]) / 0.995 + 1e-9
     autotune.reset(ks.F32)
     e2 = autotune.autotune("sort", ks.F32, n=300_000)
     assert e2["cached"] and e2["tuning"] == e["tuning"]
@@ -109,3 +110,14 @@ def test_autotuner_searches_applies_and_caches(ks, restore, tmp_path, monkeypatc
     lengths = gen.batched_lengths(128, 100, 100_000, seed=gen.seed_for(6, 12, 0))
     eb = autotune.autotune("batched", ks.F32, lengths=lengths, reps=2, max_rounds=1)
     assert eb["workload"].startswith("batched:f32:128x")
+
+
+def test_autotuner_partition_kind(ks, restore, tmp_path, monkeypatch):
+    from paper_1107_3622_gb300 import autotune
+    monkeypatch.setenv("KSORT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    e = autotune.autotune("partition", ks.F32, n=500_000, reps=2, max_rounds=1)
+    assert e["workload"] == "partition:f32:2^19"
+    # only the form of the tile passes is searched for a single partition
+    assert {c["cutoff"] for c in e["candidates"]} == {e["tuning"]["cutoff"]}
+    assert len(e["candidates"]) == len(autotune.SHAPES)
+    assert ks.ksort_get_tuning(ks.F32)["tile_shape"] == e["tuning"]["tile_shape"]
