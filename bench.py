@@ -79,6 +79,10 @@ def parse_args(argv=None):
                     help="oracle repetitions per size in --sweep (0 skips the oracle)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the library's default tuning instead of the autotuned one")
+    ap.add_argument("--tile-shape", type=int, default=0,
+                    help="fixed form of the partition passes (1..9) instead of autotuning")
+    ap.add_argument("--cutoff", type=int, default=0,
+                    help="fixed shared-memory cutoff instead of autotuning")
     ap.add_argument("--serving-requests", type=int, default=10_000,
                     help="requests of the serving run (0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
@@ -247,6 +251,15 @@ def device_source_hash():
     return h.hexdigest()[:16]
 
 
+TILE_KERNELS = {0: "tile_kernel", 1: "tile_pipe_kernel", 2: "tile_ws_kernel"}
+
+
+def tile_kernel_name(ks, dtype_code: int) -> str:
+    """`<kernel>/<form>` of the tile passes under the current tuning, e.g. tile_kernel/1."""
+    shape = ks.ksort_get_tuning(dtype_code)["tile_shape"]
+    return f"{TILE_KERNELS[ks.ksort_tile_shape(dtype_code, shape)[2]]}/{shape}"
+
+
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
     current kernel sources (else None)."""
@@ -285,8 +298,9 @@ def autotune_sort(ks, n: int, args) -> dict:
     """Tile shape, cutoff and finisher CTAs for the timed workload: the project's
     autotuner (searched in this process, on this GPU), or the defaults."""
     from paper_1107_3622_gb300 import autotune
-    if args.no_autotune:
+    if args.no_autotune or args.tile_shape or args.cutoff:
         autotune.reset(ks.F32)
+        ks.ksort_set_tuning(ks.F32, cutoff=args.cutoff, tile_shape=args.tile_shape)
         return dict(ks.ksort_get_tuning(ks.F32), autotuned=False)
     e = autotune.autotune("sort", ks.F32, n=n, reps=3)
     shape = ks.ksort_tile_shape(ks.F32, e["tuning"]["tile_shape"])
@@ -362,9 +376,10 @@ def run_ours(args, dist: Dist):
     achieved = algo_bytes / (ms_mean / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
-                "traffic": recorded_traffic("ksort_sort<float>", WORKLOAD),
-                "kernel": "ksort_sort: seed_kernel + tile_kernel<float> (tile passes) + "
-                          "small_kernel<float> (shared-memory finisher), one call",
+                "traffic": recorded_traffic(f"ksort_sort<float> {tile_kernel_name(ks, ks.F32)}",
+                                            WORKLOAD),
+                "kernel": f"ksort_sort: seed_kernel + {tile_kernel_name(ks, ks.F32)} <float> "
+                          "(tile passes) + small_kernel<float> (shared-memory finisher), one call",
                 "algorithmic_bytes_per_launch": algo_bytes,
                 "lower_bound_bytes": 2 * 4 * n,
                 "lower_bound_frac": round((2 * 4 * n) / (ms_mean / 1e3) / 1e9 / peak, 5)}
@@ -444,8 +459,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     import torch
     from paper_1107_3622_gb300 import autotune
     saved = ks.ksort_get_tuning(ks.F32)
-    if args.no_autotune:
-        autotune.reset(ks.F32)
+    if args.no_autotune or args.tile_shape or args.cutoff:
         tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=False)
     else:
         e = autotune.autotune("partition", ks.F32, n=n, reps=5)
@@ -453,6 +467,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
         tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
                      keys_per_thread=shape[1], form=shape[2], search_ms=e["ms"],
                      cached=e["cached"])
+    kname = tile_kernel_name(ks, ks.F32)
     ks.ksort_reserve_workspace(ks.F32, n, 1)
     R, reps = 8, 20
     ins = [torch.from_numpy(gen.uniform_f32(gen.seed_for(1, 6, 500 + r), n)).cuda()
@@ -480,12 +495,13 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
                         tile_shape=saved["tile_shape"])
-    return {"kernel": "ksort_partition_out: seed_kernel + tile-pass kernel of the tuned form",
+    return {"kernel": f"ksort_partition_out: seed_kernel + {kname} <float>",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),
             "peak_source": f"{peak_src} hbm_gbs",
-            "traffic": recorded_traffic("tile_kernel<float>", f"n={n} f32 rotating 8 buffers"),
+            "traffic": recorded_traffic(f"ksort_partition_out<float> {kname}",
+                                        f"n={n} f32 rotating 8 buffers"),
             "algorithmic_bytes_per_launch": 8 * n,
             "method": f"{R} buffer pairs ({2 * R * 4 * n >> 20} MiB) rotated, {reps} rounds, "
                       "CUDA events around back-to-back launches"}
@@ -499,8 +515,7 @@ def run_batched(ks, args):
     from paper_1107_3622_gb300 import autotune
     sort_tuning = ks.ksort_get_tuning(ks.F32)
     lengths = gen.batched_lengths()
-    if args.no_autotune:
-        autotune.reset(ks.F32)
+    if args.no_autotune or args.tile_shape or args.cutoff:
         tuned = {"autotuned": False}
     else:
         e = autotune.autotune("batched", ks.F32, lengths=lengths, reps=2)
