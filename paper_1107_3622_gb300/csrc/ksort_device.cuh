@@ -276,15 +276,15 @@ struct SmallShared {
   int head, tail, pending, bad, nbig, L;
 };
 
-// Steps 1-6 on a warp's worth of leaves (segments of at most 32 keys), held one key
-// per lane, several leaves side by side. With a stable partition (each side keeps the
-// order it had) the first element of every sub-array is its lowest lane, so each lane
-// only tracks the lane mask of its current sub-array and the index where that
-// sub-array starts; keys move once, to their final index, at the end.
-//   Step 1: the key is the lowest lane of the mask;
-//   Step 3: a lane goes left when !(key <= x) (ballot), else right;
-//   Step 4: the key's final index is base + #left;
-//   Steps 5-6: the left lanes keep base, the right lanes start after the key.
+// Steps 1-6 on a warp's worth of leaves (segments of at most 32 keys), one key per
+// lane, several leaves side by side. Leaf sides are kept in their order (a stable
+// partition), and for a sub-array that small the recursion of Steps 1-6 has a closed
+// form. Under the first-element key and the `key <= x` rule with order-keeping sides,
+// every key x of a leaf ends at
+//     start + #{y in the leaf : y < x} + #{y earlier in the leaf : y == x}:
+// the key of a sub-array precedes the keys equal to it (they come after it and go right),
+// and each side keeps its order. So each lane counts that index directly, with no
+// dependent chain of levels, and keys move once, to their final index.
 // Entries of `list`: start << 8 | n << 1 | parity (parity 1: the leaf is in B).
 template <typename K>
 __device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *list, int count) {
@@ -308,32 +308,21 @@ __device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *
   const int lo = __shfl_sync(kFull, off, leaf);
   const int n = (int)((e >> 1) & 127u);
   const int s0 = (int)(e >> 8);
+  const K *src = ((e & 1u) ? B : A) + s0;
+  const int me = lane - lo;
   K x = K(0);
-  if (act) x = (e & 1u) ? B[s0 + lane - lo] : A[s0 + lane - lo];
-  unsigned mask = act ? (((n >= 32) ? kFull : ((1u << n) - 1u)) << lo) : 0u;
-  int base = s0;
-  for (int level = 0; level < 32; ++level) {
-    const bool big = act && (mask & (mask - 1u)) != 0u;
-    if (!__any_sync(kFull, big)) break;
-    const int piv = __ffs(mask) - 1;
-    const K key = __shfl_sync(kFull, x, piv < 0 ? 0 : piv);
-    const bool is_key = lane == piv;
-    const bool lf = big && !is_key && goes_left(key, x);
-    const unsigned low = __ballot_sync(kFull, lf) & mask;
-    if (big) {
-      const int Lc = __popc(low);
-      if (is_key) {
-        base += Lc;
-        mask = 1u << lane;
-      } else if (lf) {
-        mask = low;
-      } else {
-        base += Lc + 1;
-        mask &= ~(low | (1u << piv));
-      }
+  int pos = 0;
+  if (act) {
+    x = src[me];
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) {
+      const K y = src[j];
+      // y < x (y goes left of key x), or y == x and y comes earlier
+      pos += (goes_left(x, y) || (j < me && !goes_left(y, x))) ? 1 : 0;
     }
   }
-  if (act) A[base] = x;
+  __syncwarp();  // every lane has read its leaf before any key moves
+  if (act) A[s0 + pos] = x;
   __syncwarp();
 }
 
