@@ -495,7 +495,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
                         tile_shape=saved["tile_shape"])
-    return {"kernel": f"ksort_partition_out: seed_kernel + {kname} <float>",
+    return {"kernel": f"ksort_partition_out: part_kernel<float> (CTA shape of {kname})",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),

@@ -71,7 +71,11 @@ KSORT_API ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, in
                                int64_t *key_index_dev, ksort_stream_t stream);
 
 /* The same partition, out of place: in_dev is read, out_dev (n keys, not overlapping
- * in_dev) receives the partitioned keys. One read and one write pass over the keys. */
+ * in_dev) receives the partitioned keys. One launch, one read and one write pass over the
+ * keys: CTAs take the tiles round-robin, stage each next tile into shared memory by a
+ * bulk copy, chain the tiles' less counts by decoupled look-back, and write each tile's
+ * two sides to the front and the back of out_dev. The CTA shape is that of the tuned
+ * tile_shape (see ksort_set_tuning). */
 KSORT_API ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
                                    int64_t n, int64_t *key_index_dev, ksort_stream_t stream);
 

@@ -201,8 +201,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 
     best_ms = measure(best)
     axes = (("tile_shape", SHAPES), ("cutoff", cutoffs), ("ctas_per_sm", FINISHER_CTAS))
-    if kind == "partition":  # a single partition runs tile passes only
-        axes = axes[:1]
+    if kind == "partition":  # one part_kernel launch: only its CTA shape matters
+        axes = (("tile_shape", SHAPES[:3]),)
     for _ in range(max_rounds):
         improved = False
         for name, values in axes:

@@ -43,13 +43,15 @@ struct Ops {
   cudaError_t (*tiles)(const SortParams &, int, int, cudaStream_t);
   cudaError_t (*smalls)(const SortParams &, int, cudaStream_t);
   long long (*tile_count)(int, const void *, long long, long long);
+  cudaError_t (*part_occupancy)(int, int *);
+  cudaError_t (*partition)(const SortParams &, int, int, cudaStream_t);
 };
 
 template <typename K>
 Ops ops_for() {
-  return Ops{&Launcher<K>::info,   &Launcher<K>::small_smem_bytes, &Launcher<K>::occupancy,
-             &Launcher<K>::seed,   &Launcher<K>::tiles,            &Launcher<K>::smalls,
-             &Launcher<K>::tile_count};
+  return Ops{&Launcher<K>::info,       &Launcher<K>::small_smem_bytes, &Launcher<K>::occupancy,
+             &Launcher<K>::seed,       &Launcher<K>::tiles,            &Launcher<K>::smalls,
+             &Launcher<K>::tile_count, &Launcher<K>::part_occupancy,   &Launcher<K>::partition};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -236,6 +238,23 @@ ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g)
   return KSORT_OK;
 }
 
+std::map<std::pair<int, int>, int> g_part_occ;  // (dtype, shape) -> part_kernel CTAs per SM
+
+ksort_status_t part_occupancy(ksort_dtype_t dt, int shape, int *occ) {
+  auto key = std::make_pair((int)dt, shape);
+  auto it = g_part_occ.find(key);
+  if (it != g_part_occ.end()) {
+    *occ = it->second;
+    return KSORT_OK;
+  }
+  int o = 0;
+  KS_CUDA(ops(dt).part_occupancy(shape, &o));
+  if (o < 1) return KSORT_ERR_INTERNAL;
+  g_part_occ[key] = o;
+  *occ = o;
+  return KSORT_OK;
+}
+
 SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
   SortParams p{};
   p.keys = keys;
@@ -289,12 +308,16 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
     if (!in_place) KS_CUDA(cudaMemcpyAsync(dst, in, kb, cudaMemcpyDeviceToDevice, s));
     return KSORT_OK;
   }
-  // One item that only runs Steps 1-4: buffer 0 is read, buffer 1 receives the result.
-  const long long tiles = ops(dt).tile_count(tu.variant, in, 0, n);
+  // One launch of part_kernel (the CTA shape of the tuned form): buffer 0 is read,
+  // buffer 1 receives the result.
+  const int shape = tu.variant % kTileShapes;
+  const long long tiles = ops(dt).tile_count(shape, in, 0, n);  // form-0 variants: plain tiles
   if ((unsigned long long)tiles > ws->lb_cap) return KSORT_ERR_INVALID_ARG;
-  Grids g{};
-  if ((st = full_grids(dt, dev, tu, &g)) != KSORT_OK) return st;
-  const int grid = (int)std::max<long long>(1, std::min<long long>(g.tiles, tiles));
+  int occ = 0;
+  if ((st = part_occupancy(dt, shape, &occ)) != KSORT_OK) return st;
+  int sms = 0;
+  if ((st = device_sms(dev, &sms)) != KSORT_OK) return st;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * occ, tiles));
   SortParams p = sort_params(*ws, const_cast<void *>(in), tu);
   p.scratch = dst;
   p.num_roots = 1;
@@ -303,8 +326,7 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   p.key_index = reinterpret_cast<long long *>(key_index);
   p.readable[0] = n;
   p.readable[1] = 0;  // buffer 1 is only written
-  KS_CUDA(ops(dt).seed(p, tu.variant, s));
-  KS_CUDA(ops(dt).tiles(p, tu.variant, grid, s));
+  KS_CUDA(ops(dt).partition(p, shape, grid, s));
   if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
   return KSORT_OK;
 }

@@ -30,6 +30,9 @@ constexpr int kSmallWarps = kSmallThreads / 32;
 #ifndef KSORT_LOOKBACK_PER
 #define KSORT_LOOKBACK_PER 1
 #endif
+#ifndef KSORT_PART_LOOKBACK_PER
+#define KSORT_PART_LOOKBACK_PER 1  // part_kernel: windows of 32 x this many descriptors
+#endif
 // tile_kernel CTAs per SM that the register budget is sized for (64 registers a thread)
 constexpr int tile_min_blocks(int nt) { return 1024 / nt; }
 
@@ -140,12 +143,12 @@ __device__ __forceinline__ unsigned long long lb_pack(unsigned epoch, bool inclu
 // bounded by `limit_ns`. Returns 0 when the prefix was found, 1 on timeout, 2 when the
 // call was aborted.
 constexpr int kLookbackPer = KSORT_LOOKBACK_PER;
+template <int PER = kLookbackPer>
 __device__ __forceinline__ int lookback(const unsigned long long *lb, unsigned t, unsigned epoch,
                                         unsigned long long limit_ns, const unsigned *abort_flag,
                                         unsigned long long *E_out,
                                         unsigned long long *steps,
                                         unsigned long long *dbg = nullptr) {
-  constexpr int PER = kLookbackPer;
   constexpr int NONE = 32 * PER;
   const int lane = threadIdx.x & 31;
   unsigned long long E = 0;
@@ -212,32 +215,58 @@ __device__ __forceinline__ int lookback(const unsigned long long *lb, unsigned t
   }
 }
 
-// Writes count keys from shared memory (sm[0..count)) to global g[0..count) with the NT
-// threads of the CTA: scalar stores up to the first 16-byte boundary of g, then one
-// 128-bit store per vector.
-template <typename K, int NT>
-__device__ __forceinline__ void copy_out(const K *sm, K *g, unsigned count) {
+// Writes count keys from shared memory so[0..count) to global g[0..count) with NG
+// threads (rank r): scalar stores up to g's first 16-byte boundary, then one 128-bit
+// store per vector. Every vector is assembled from the two aligned 16-byte chunks of
+// shared memory it straddles (all vectors of a call have the same misalignment), so the
+// shared-memory reads are whole chunks and do not collide in banks. The reads may touch
+// up to 16 bytes past so[count): every buffer passed here carries that much room.
+template <typename K, int NG>
+__device__ __forceinline__ void copy_out_v(const K *so, K *g, unsigned count, int r) {
   constexpr int VEC = Vec<K>::N;
   using V = typename Vec<K>::T;
-  const int tid = threadIdx.x;
   unsigned head = (unsigned)(((16u - (reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) / sizeof(K));
   if (head > count) head = count;
-  if (tid < (int)head) g[tid] = sm[tid];
+  if (r < (int)head) g[r] = so[r];
   const unsigned nvec = (count - head) / VEC;
   V *gv = reinterpret_cast<V *>(g + head);
-  for (unsigned v = tid; v < nvec; v += NT) {
-    K x[VEC];
-#pragma unroll
-    for (int l = 0; l < VEC; ++l) x[l] = sm[head + v * VEC + l];
-    V q;
-    if constexpr (VEC == 4) {
-      q.x = x[0]; q.y = x[1]; q.z = x[2]; q.w = x[3];
-    } else {
-      q.x = x[0]; q.y = x[1];
+  const K *s0 = so + head;
+  const unsigned mis = (unsigned)((reinterpret_cast<uintptr_t>(s0) & 15u) / sizeof(K));
+  const V *cv = reinterpret_cast<const V *>(s0 - mis);
+  for (unsigned v = r; v < nvec; v += NG) {
+    const V a = cv[v];
+    V q = a;
+    if (mis != 0) {
+      const V b = cv[v + 1];
+      if constexpr (VEC == 4) {
+        if (mis == 1) { q.x = a.y; q.y = a.z; q.z = a.w; q.w = b.x; }
+        else if (mis == 2) { q.x = a.z; q.y = a.w; q.z = b.x; q.w = b.y; }
+        else { q.x = a.w; q.y = b.x; q.z = b.y; q.w = b.z; }
+      } else {
+        q.x = a.y;
+        q.y = b.x;
+      }
     }
     gv[v] = q;
   }
-  for (unsigned k = head + nvec * VEC + tid; k < count; k += NT) g[k] = sm[k];
+  for (unsigned k = head + nvec * VEC + r; k < count; k += NG) g[k] = so[k];
+}
+
+// Scatter of one thread's IPT keys into a tile's output (bit j of lessbits / gebits: key
+// j goes to the less / >= side), thread by thread: wl0 / wg0 are the output indices of
+// the warp's first less / >= key and `excl` packs this thread's exclusive counts within
+// the warp (less in the low, >= in the high 16 bits). (A slot-major order, conflict-free
+// in shared memory, measured slower: its ballots cost more than the bank conflicts.)
+template <typename K, int IPT>
+__device__ __forceinline__ void scatter_keys(K *so, const K (&x)[IPT], unsigned lessbits,
+                                             unsigned gebits, unsigned wl0, unsigned wg0,
+                                             unsigned excl) {
+  unsigned rl = wl0 + (excl & 0xffffu), rg = wg0 + (excl >> 16);
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    if ((lessbits >> j) & 1u) so[rl++] = x[j];
+    else if ((gebits >> j) & 1u) so[rg++] = x[j];
+  }
 }
 
 // Global offsets of the two sides of tile t; false (and an error) if inconsistent.
@@ -580,7 +609,7 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
     if (nleaves) warp_leaf_run(A, B, leaves, nleaves);
   }
   bsync();
-  copy_out<K, kSmallThreads>(A, out, (unsigned)m);
+  copy_out_v<K, kSmallThreads>(A, out, (unsigned)m, tid);
   if (tid == 0) *segments += nseg;
   return q.bad == 0;
 }
@@ -780,7 +809,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
   constexpr int NW = NT / 32;
   static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0, "bad tile shape");
   using V = typename Vec<K>::T;
-  __shared__ __align__(16) K sout[TILE];
+  __shared__ __align__(16) K sout[TILE + Vec<K>::N];  // + room for copy_out_v's reads
   __shared__ TileCtaShared<NW> sh;
   K *const buf0 = static_cast<K *>(p.keys);
   K *const buf1 = static_cast<K *>(p.scratch);
@@ -925,16 +954,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
         trace_mark(p, sh.k, 3);  // look-back done
       }
     }
-    {
-      const unsigned excl = incl - mine;
-      unsigned rl = wlx + (excl & 0xffffu);
-      unsigned rg = L + wgx + (excl >> 16);
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        if ((lessbits >> j) & 1u) sout[rl++] = x[j];
-        else if ((gebits >> j) & 1u) sout[rg++] = x[j];
-      }
-    }
+    scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
     __syncthreads();
     const unsigned long long E = sh.E;
     if (sh.abort) break;
@@ -945,8 +965,8 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       if (tid == 0) raise_error(ctl, kDevInternal, 0x500000000ull | t);
       break;
     }
-    copy_out<K, NT>(sout, dst + lbase, L);
-    copy_out<K, NT>(sout + L, dst + gbase, G);
+    copy_out_v<K, NT>(sout, dst + lbase, L, tid);
+    copy_out_v<K, NT>(sout + L, dst + gbase, G, tid);
     __syncthreads();
 
     // ---- completion: the last tile of the item places the key and queues both sides
@@ -1159,7 +1179,7 @@ __device__ __forceinline__ unsigned long long tmap_probe(const SortParams &p,
 }
 
 template <typename K, int TILE>
-constexpr size_t pipe_smem_bytes() { return (size_t)3 * TILE * sizeof(K); }
+constexpr size_t pipe_smem_bytes() { return (size_t)3 * TILE * sizeof(K) + 16; }  // + copy_out_v room
 
 // Phase 1, staged form of tile_kernel: the same tile passes, Steps and output, with the
 // keys of the next tile already in shared memory when a tile starts. A CTA owns two
@@ -1314,16 +1334,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
         trace_mark(p, sh.cur.k, 3);
       }
     }
-    {
-      const unsigned excl = incl - mine;
-      unsigned rl = wlx + (excl & 0xffffu);
-      unsigned rg = L + wgx + (excl >> 16);
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        if ((lessbits >> j) & 1u) sout[rl++] = x[j];
-        else if ((gebits >> j) & 1u) sout[rg++] = x[j];
-      }
-    }
+    scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
     if (w > 0 && ns0 == kPipeCopying) {
       // the next tile's copy was started a tile period ago: count it if it has landed
       // sh.fail and sh.early_L were cleared before the CTA barrier that ended the last tile
@@ -1369,8 +1380,8 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
     }
 
     // ---- write
-    copy_out<K, NT>(sout, dst + lbase, L);
-    copy_out<K, NT>(sout + L, dst + gbase, G);
+    copy_out_v<K, NT>(sout, dst + lbase, L, tid);
+    copy_out_v<K, NT>(sout + L, dst + gbase, G, tid);
     __syncthreads();
 
     // ---- completion (thread 0), and the next copies into the buffers no longer needed
@@ -1517,31 +1528,6 @@ __device__ __forceinline__ bool mbar_wait_or_abort(unsigned long long *bar, unsi
   }
 }
 
-// copy_out for a group of NG threads (rank r) instead of the whole CTA.
-template <typename K, int NG>
-__device__ __forceinline__ void copy_out_group(const K *sm, K *g, unsigned count, int r) {
-  constexpr int VEC = Vec<K>::N;
-  using V = typename Vec<K>::T;
-  unsigned head = (unsigned)(((16u - (reinterpret_cast<uintptr_t>(g) & 15u)) & 15u) / sizeof(K));
-  if (head > count) head = count;
-  if (r < (int)head) g[r] = sm[r];
-  const unsigned nvec = (count - head) / VEC;
-  V *gv = reinterpret_cast<V *>(g + head);
-  for (unsigned v = r; v < nvec; v += NG) {
-    K x[VEC];
-#pragma unroll
-    for (int l = 0; l < VEC; ++l) x[l] = sm[head + v * VEC + l];
-    V q;
-    if constexpr (VEC == 4) {
-      q.x = x[0]; q.y = x[1]; q.z = x[2]; q.w = x[3];
-    } else {
-      q.x = x[0]; q.y = x[1];
-    }
-    gv[v] = q;
-  }
-  for (unsigned k = head + nvec * VEC + r; k < count; k += NG) g[k] = sm[k];
-}
-
 // A tile staged in one input buffer (written by the load warp before its copy starts).
 struct WsTile {
   Item it;
@@ -1583,7 +1569,7 @@ constexpr int kWsBarStart = 1, kWsBarData = 2, kWsBarCnt = 3 /* and 4 */, kWsBar
               kWsBarWritten = 7;
 
 template <typename K, int TILE>
-constexpr size_t ws_smem_bytes() { return (size_t)3 * TILE * sizeof(K); }
+constexpr size_t ws_smem_bytes() { return (size_t)3 * TILE * sizeof(K) + 16; }  // + copy_out_v room
 
 // Phase 1, warp-specialised form of tile_kernel: the same tile passes, Steps and
 // output, by three groups of warps of one CTA that wait on each other only through
@@ -1886,16 +1872,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_ws_kernel(SortPa
     else nbar_arrive(kWsBarCnt, NTD + 32);
     // ---- scatter into the output tile (its last readers wrote it out before the data
     // warps reached kWsBarData above)
-    {
-      const unsigned excl = incl - mine;
-      unsigned rl = wlx + (excl & 0xffffu);
-      unsigned rg = L + wgx + (excl >> 16);
-#pragma unroll
-      for (int jx = 0; jx < IPT; ++jx) {
-        if ((lessbits >> jx) & 1u) sout0[rl++] = x[jx];
-        else if ((gebits >> jx) & 1u) sout0[rg++] = x[jx];
-      }
-    }
+    scatter_keys<K, IPT>(sout0, x, lessbits, gebits, wlx, L + wgx, incl - mine);
     // ---- while the look-back runs: count the next tile early if its keys have landed,
     // and publish its aggregate, so that later tiles' look-backs find it sooner
     {
@@ -1948,12 +1925,263 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_ws_kernel(SortPa
       // impossible prefixes: record, and write nothing (the other warps decide the same)
       if (dt == 0) raise_error(ctl, kDevInternal, 0x500000000ull | rc.t);
     } else {
-      copy_out_group<K, NTD>(sout0, dst + lbase, L, dt);
-      copy_out_group<K, NTD>(sout0 + L, dst + gbase, G, dt);
+      copy_out_v<K, NTD>(sout0, dst + lbase, L, dt);
+      copy_out_v<K, NTD>(sout0 + L, dst + gbase, G, dt);
     }
     nbar_arrive(kWsBarWritten, NTD + 32);
     par ^= 1;
     b ^= 1;
+  }
+}
+
+// ----------------------------------------------------------------------------- partition
+// One partition (Steps 1-4) of buffer 0's [0, total) into buffer 1, in a single launch
+// and without the work queue: CTA c handles tiles c, c + G, c + 2G, ... of the one item,
+// so every CTA knows its next tile in advance and stages it into shared memory by a bulk
+// copy while the current tile is finished. Per tile: count in shared memory (Step 3),
+// publish the aggregate, decoupled look-back by warp 0 while the other warps scatter and
+// count the CTA's next tile early (publishing its aggregate too), then write both sides.
+// The tile that holds the last keys learns the total less count from its own look-back
+// and places the key there (Step 4): no per-tile completion count is needed.
+// The generation (epoch) is the workspace's next one; the last CTA to finish makes it
+// the current one and clears the partition's own stop flag and CTA count.
+// Dynamic shared memory: two input tiles and the output tile.
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) part_kernel(SortParams p) {
+  constexpr int TILE = NT * IPT;
+  constexpr int VEC = Vec<K>::N;
+  constexpr int NV = IPT / VEC;
+  constexpr int NW = NT / 32;
+  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0 && NW > 1, "bad tile shape");
+  using V = typename Vec<K>::T;
+  extern __shared__ __align__(128) unsigned char part_smem[];
+  K *const sin0 = reinterpret_cast<K *>(part_smem);
+  K *const sout = sin0 + 2 * TILE;
+  __shared__ unsigned wl[NW], wg[NW];
+  __shared__ unsigned long long bar[2];
+  __shared__ unsigned long long sE;
+  __shared__ int sabort, sfail;
+  __shared__ unsigned early_L;
+  Control *ctl = p.ctl;
+  unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch) + 1u;
+  if (epoch == 0u || epoch >= kMaxEpoch) epoch = 1u;
+  const K *const src = static_cast<const K *>(p.keys);
+  K *const dst = static_cast<K *>(p.scratch);
+  const long long n = p.total;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int G = gridDim.x;
+  const long long base = tile_base(src, 0);  // the key is src[0]; tiles start here
+  const long long tiles = (n - base + TILE - 1) / TILE;
+  const K key = __ldcg(src);  // Step 1: the first element is the key
+  unsigned long long *lb = p.lb;
+  unsigned long long st_lb = 0;
+
+  auto geom = [&](long long t, int *vlo, int *vhi, long long *lo) {
+    *lo = base + t * TILE;
+    *vlo = (int)(1 > *lo ? 1 - *lo : 0);
+    *vhi = (int)(n - *lo < TILE ? n - *lo : TILE);
+  };
+  auto issue = [&](long long t, int j) {
+    int vlo, vhi;
+    long long lo;
+    geom(t, &vlo, &vhi, &lo);
+    const unsigned bytes = (unsigned)((vhi + VEC - 1) / VEC * VEC) * (unsigned)sizeof(K);
+    fence_proxy_async();
+    mbar_expect_tx(&bar[j], bytes);
+    bulk_g2s(sin0 + j * TILE, src + lo, bytes, &bar[j]);
+  };
+
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    sfail = 0;
+    early_L = 0;
+    if (blockIdx.x < tiles) issue(blockIdx.x, 0);
+    if (blockIdx.x + G < tiles) issue(blockIdx.x + G, 1);
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  int b = 0, early = 0;
+  // on a stop, the copies still in flight: this tile's (if it never landed) and the next
+  int drain_cur = 0, drain_next = 0;
+  for (long long t = blockIdx.x; t < tiles; t += G) {
+    if (tid == 0) trace_mark(p, (unsigned long long)t, 0);  // tile starts
+    const bool landed = mbar_wait(&bar[b], (phase >> b) & 1u, p.spin_limit_ns);
+    phase ^= 1u << b;
+    if (tid == 0) trace_mark(p, (unsigned long long)t, 1);  // keys in shared memory
+    int vlo, vhi;
+    long long lo;
+    geom(t, &vlo, &vhi, &lo);
+    const K *sin = sin0 + b * TILE;
+    K x[IPT];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const V q = *reinterpret_cast<const V *>(sin + (v * NT + tid) * VEC);
+      if constexpr (VEC == 4) {
+        x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
+      } else {
+        x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
+      }
+    }
+    unsigned lessbits = 0, gebits = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        const int jx = v * VEC + l, kk = (v * NT + tid) * VEC + l;
+        const bool valid = kk >= vlo && kk < vhi;
+        const bool le = goes_left(key, x[jx]);
+        lessbits |= (unsigned)(valid && le) << jx;
+        gebits |= (unsigned)(valid && !le) << jx;
+      }
+    }
+    const unsigned mine = (unsigned)__popc(lessbits) | ((unsigned)__popc(gebits) << 16);
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned u = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) {
+      wl[w] = incl & 0xffffu;
+      wg[w] = incl >> 16;
+    }
+    const bool has_next = t + G < tiles;
+    if (__syncthreads_or(!landed)) {
+      if (tid == 0) {
+        raise_error(ctl, kDevTimeout, 0x900000000ull | (unsigned)t);
+        atomicExch(&ctl->part_abort, 1u);
+      }
+      drain_cur = landed ? 0 : 1;
+      drain_next = has_next ? 1 : 0;
+      break;
+    }
+    unsigned L = 0, Gc = 0, wlx = 0, wgx = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      const unsigned a = wl[i], c = wg[i];
+      if (i < w) {
+        wlx += a;
+        wgx += c;
+      }
+      L += a;
+      Gc += c;
+    }
+    const unsigned tt = (unsigned)t;
+    if (tid == 0 && !early) st_relaxed(&lb[tt], lb_pack(epoch, tt == 0, L));
+    if (tid == 0) trace_mark(p, (unsigned long long)t, 2);  // counted
+    if (w == 0) {
+      unsigned long long E = 0;
+      int status = 0;
+      if (tt > 0) {
+        unsigned long long steps = 0;
+        // (measured: wider windows cost more than the steps they save)
+        status = lookback<KSORT_PART_LOOKBACK_PER>(lb, tt, epoch, p.spin_limit_ns,
+                                                   &ctl->part_abort, &E, &steps);
+        if (lane == 0) {
+          if (status == 0) st_relaxed(&lb[tt], lb_pack(epoch, true, (unsigned)(E + L)));
+          st_lb += steps;
+        }
+      }
+      if (lane == 0) {
+        if (status == 1) {
+          raise_error(ctl, kDevTimeout, 0x100000000ull | tt);
+          atomicExch(&ctl->part_abort, 1u);
+        }
+        sE = E;
+        sabort = status == 0 ? 0 : 1;
+        trace_mark(p, (unsigned long long)t, 3);  // look-back done
+      }
+    }
+    scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
+    // the other warps: count the next tile early if its keys have landed
+    const long long tn = t + G;
+    early = 0;
+    if (w > 0 && tn < tiles) {
+      const bool ok = mbar_test(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
+      if (__all_sync(kFull, ok)) {
+        int nvlo, nvhi;
+        long long nlo;
+        geom(tn, &nvlo, &nvhi, &nlo);
+        const K *snx = sin0 + (b ^ 1) * TILE;
+        unsigned cnt = 0;
+        for (int v = tid - 32; v < TILE / VEC; v += NT - 32) {
+          const V q = *reinterpret_cast<const V *>(snx + v * VEC);
+          K y[VEC];
+          if constexpr (VEC == 4) {
+            y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
+          } else {
+            y[0] = q.x; y[1] = q.y;
+          }
+#pragma unroll
+          for (int l = 0; l < VEC; ++l) {
+            const int kk = v * VEC + l;
+            cnt += (kk >= nvlo && kk < nvhi && goes_left(key, y[l])) ? 1u : 0u;
+          }
+        }
+        cnt = __reduce_add_sync(kFull, cnt);
+        if (lane == 0) atomicAdd(&early_L, cnt);
+      } else if (lane == 0) {
+        sfail = 1;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");
+      if (tid == 32 && !sfail) {
+        st_relaxed(&lb[(unsigned)tn], lb_pack(epoch, (unsigned)tn == 0, early_L));
+        trace_mark(p, (unsigned long long)tn, 5);  // aggregate published early
+      }
+    }
+    __syncthreads();
+    if (tn < tiles) early = !sfail;  // the same value in every thread
+    if (sabort) {
+      drain_next = has_next ? 1 : 0;
+      break;
+    }
+    const unsigned long long E = sE;
+    // write: less keys from the front, >= keys from the back (the key's slot stays free)
+    const long long PV = tt == 0 ? 0 : lo - 1;  // classified keys in earlier tiles
+    const long long lbase = (long long)E, gbase = n - (PV - (long long)E) - (long long)Gc;
+    if (lbase < 0 || lbase + L > n || gbase < 1 || gbase + Gc > n) {
+      if (tid == 0) {
+        raise_error(ctl, kDevInternal, 0x500000000ull | tt);
+        atomicExch(&ctl->part_abort, 1u);
+      }
+      drain_next = has_next ? 1 : 0;
+      break;
+    }
+    copy_out_v<K, NT>(sout, dst + lbase, L, tid);
+    copy_out_v<K, NT>(sout + L, dst + gbase, Gc, tid);
+    if (t == tiles - 1 && tid == 0) {
+      const long long c = (long long)E + L;  // #{x < key}: Step 4
+      dst[c] = key;
+      if (p.key_index) *p.key_index = c;
+    }
+    // this buffer takes the tile after next (once every thread is done reading it)
+    __syncthreads();
+    if (tid == 0) {
+      trace_mark(p, (unsigned long long)t, 4);  // written
+      if (p.trace && (unsigned long long)t < (unsigned long long)p.trace_cap)
+        p.trace[t * kTraceWords + 7] = blockIdx.x;
+      sfail = 0;
+      early_L = 0;
+      if (t + 2 * (long long)G < tiles) issue(t + 2 * G, b);
+    }
+    b ^= 1;
+  }
+  // copies still in flight land before the CTA leaves (bounded); after a normal end none is
+  if (tid == 0) {
+    if (drain_cur) mbar_wait(&bar[b], ((phase >> b) & 1u) ^ 1u, p.spin_limit_ns);
+    if (drain_next) mbar_wait(&bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
+  }
+  if (tid == 0) {
+    if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
+    __threadfence();
+    if (atomicAdd(&ctl->part_done, 1u) == (unsigned)G - 1u) {
+      // every CTA has read the epoch: the next call gets the one after
+      ctl->part_done = 0u;
+      ctl->part_abort = 0u;
+      ctl->epoch = epoch;
+    }
   }
 }
 

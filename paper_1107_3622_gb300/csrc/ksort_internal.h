@@ -46,7 +46,10 @@ struct alignas(128) Control {
   // statistics of the last sort
   unsigned long long large_items, large_keys, tiles, small_items, small_keys;
   unsigned long long smem_levels, lookback_steps;
-  unsigned long long pad1[3];
+  // single-partition kernel: CTAs finished, and its own stop flag (both back to 0 when
+  // the last CTA of a call finishes)
+  unsigned part_done, part_abort;
+  unsigned long long pad1[2];
 };
 
 // One work item: a sub-array [begin, end) whose first element is its key.
@@ -115,6 +118,9 @@ struct Launcher {
   static cudaError_t tiles(const SortParams &p, int variant, int grid, cudaStream_t s);
   static cudaError_t smalls(const SortParams &p, int grid, cudaStream_t s);
   static long long tile_count(int variant, const void *buf, long long begin, long long end);
+  // single partitions: part_kernel with CTA shape `shape` (0 .. kTileShapes - 1)
+  static cudaError_t part_occupancy(int shape, int *ctas);
+  static cudaError_t partition(const SortParams &p, int shape, int grid, cudaStream_t s);
 };
 
 }  // namespace ksort

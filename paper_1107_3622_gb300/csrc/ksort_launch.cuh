@@ -137,6 +137,42 @@ cudaError_t Launcher<K>::tiles(const SortParams &p, int variant, int grid, cudaS
   });
 }
 
+// part_kernel of CTA shape `shape`, with its dynamic shared memory allowed.
+template <typename K, typename S>
+cudaError_t part_kernel_of(void (**fn)(SortParams), size_t *smem) {
+  *fn = dev::part_kernel<K, S::NT, S::IPT>;
+  *smem = dev::pipe_smem_bytes<K, S::NT * S::IPT>();
+  cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename K>
+cudaError_t Launcher<K>::part_occupancy(int shape, int *ctas) {
+  return with_shape<K>(shape % kTileShapes, [&](auto s) {
+    using S = decltype(s);
+    void (*fn)(SortParams) = nullptr;
+    size_t smem = 0;
+    cudaError_t e = part_kernel_of<K, S>(&fn, &smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, S::NT, smem);
+  });
+}
+
+template <typename K>
+cudaError_t Launcher<K>::partition(const SortParams &p, int shape, int grid, cudaStream_t st) {
+  return with_shape<K>(shape % kTileShapes, [&](auto s) {
+    using S = decltype(s);
+    void (*fn)(SortParams) = nullptr;
+    size_t smem = 0;
+    cudaError_t e = part_kernel_of<K, S>(&fn, &smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, S::NT, smem, st>>>(p);
+    return cudaGetLastError();
+  });
+}
+
 template <typename K>
 cudaError_t Launcher<K>::smalls(const SortParams &p, int grid, cudaStream_t s) {
   auto sk = dev::small_kernel<K>;
