@@ -467,7 +467,8 @@ def run_partition_pass(ks, n, peak, peak_src, args):
         tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
                      keys_per_thread=shape[1], form=shape[2], search_ms=e["ms"],
                      cached=e["cached"])
-    kname = tile_kernel_name(ks, ks.F32)
+    nt, ipt, _ = ks.ksort_tile_shape(ks.F32, ks.ksort_get_tuning(ks.F32)["tile_shape"])
+    kname = f"part_kernel<{nt}x{ipt}>"
     ks.ksort_reserve_workspace(ks.F32, n, 1)
     R, reps = 8, 20
     ins = [torch.from_numpy(gen.uniform_f32(gen.seed_for(1, 6, 500 + r), n)).cuda()
@@ -495,7 +496,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
                         tile_shape=saved["tile_shape"])
-    return {"kernel": f"ksort_partition_out: part_kernel<float> (CTA shape of {kname})",
+    return {"kernel": f"ksort_partition_out: {kname} <float>, one launch",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),
