@@ -11,6 +11,8 @@ Also reported on the same line:
   e2e            the same metric with host buffers (pinned H2D + sort + D2H timed)
   cpu_baseline   the C oracle on this host's cores, single thread, bounded sample
   partition_pass ksort_partition_out alone at the same size (buffers rotated > L2)
+  exact_partition ksort_partition_exact (the paper's element order) at the same size,
+                 checked byte for byte against the oracle
   batched        4096 log-uniform arrays: one graph-replayed ksort_sort_batched vs a
                  loop of per-array ksort_sort launches
   serving        10,000 Poisson requests (log-uniform 1e3..1e7 keys, half float32, half
@@ -70,8 +72,8 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=N_KEYS)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra (partition_pass, batched, serving, cpu_baseline)")
-    ap.add_argument("--extras", default="partition,batched,serving,cpu",
-                    help="comma-separated extras to run: partition, batched, serving, cpu")
+    ap.add_argument("--extras", default="partition,exact,batched,serving,cpu",
+                    help="comma-separated extras to run: partition, exact, batched, serving, cpu")
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the headline line: the Table 1 size sweep (float32 and "
                          "float64, 20 repetitions per size) as one JSON line")
@@ -412,6 +414,8 @@ def run_ours(args, dist: Dist):
     if dist.rank == 0:
         if "partition" in extras:
             line["partition_pass"] = run_partition_pass(ks, n, peak, peak_src, args)
+        if "exact" in extras:
+            line["exact_partition"] = run_exact_partition(ks, n, peak, peak_src)
         if "batched" in extras:
             line["batched"] = run_batched(ks, args)
         if "serving" in extras and args.serving_requests > 0:
@@ -506,6 +510,42 @@ def run_partition_pass(ks, n, peak, peak_src, args):
             "algorithmic_bytes_per_launch": 8 * n,
             "method": f"{R} buffer pairs ({2 * R * 4 * n >> 20} MiB) rotated, {reps} rounds, "
                       "CUDA events around back-to-back launches"}
+
+
+def run_exact_partition(ks, n, peak, peak_src):
+    """ksort_partition_exact (the paper's element order) at the same size, 8 rotating
+    input/output pairs; checked byte for byte against the oracle on one of them."""
+    import torch
+    import oracle
+    R, reps = 8, 10
+    ins = [torch.from_numpy(gen.uniform_f32(gen.seed_for(1, 6, 700 + r), n)).cuda()
+           for r in range(R)]
+    outs = [torch.empty_like(x) for x in ins]
+    idx = torch.empty(R, dtype=torch.int64, device="cuda")
+    for r in range(R):
+        ks.ksort_partition_exact(ks.F32, ins[r], outs[r], n, idx[r:r + 1])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        for r in range(R):
+            ks.ksort_partition_exact(ks.F32, ins[r], outs[r], n, idx[r:r + 1])
+    e1.record()
+    torch.cuda.synchronize()
+    if ks.ksort_get_device_error():
+        raise RuntimeError("device error in the exact partition")
+    ms = e0.elapsed_time(e1) / (R * reps)
+    a = ins[0].cpu().numpy()
+    want = a.copy()
+    ri, *_ = oracle.partition(want)
+    same = bool(int(idx[0].item()) == ri and outs[0].cpu().numpy().tobytes() == want.tobytes())
+    gbs = 2 * 4 * n / (ms / 1e3) / 1e9
+    return {"kernel": "ksort_partition_exact: exact_count + exact_scan + exact_rank + "
+                      "exact_place <float>", "n": n, "us_per_launch": round(ms * 1e3, 2),
+            "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": 8 * n,
+            "identical_to_oracle": same, "gpu_launches_per_call": 4,
+            "method": f"{R} buffer pairs rotated, {reps} rounds, CUDA events"}
 
 
 def run_batched(ks, args):

@@ -79,6 +79,20 @@ KSORT_API ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, in
 KSORT_API ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
                                    int64_t n, int64_t *key_index_dev, ksort_stream_t stream);
 
+/* Steps 1-4 once, out of place, in the paper's own element order (Section 1.1, Steps 1-4):
+ * out_dev receives exactly the array the paper's hole scheme (temp, flag, the front and
+ * back holes) leaves behind, not only the same key index and sides. That scheme has a
+ * closed form. Take the elements after the key in order, let F_t be the t-th one >= key
+ * from the front and B_t the t-th one < key from the back, and let T count the t with F_t
+ * before B_t. Then B_t swaps places with F_t as the holes move, and F_0 ends at i + 1
+ * (temp). The call computes it in four passes: tile counts, their scan, per-element
+ * ranks and placement. Same arguments and checks as ksort_partition_out; the workspace
+ * of (current device, stream) holds two int32 index arrays of n entries. It is meant for
+ * layout-level checks, not for speed. */
+KSORT_API ksort_status_t ksort_partition_exact(ksort_dtype_t dtype, const void *in_dev,
+                                               void *out_dev, int64_t n,
+                                               int64_t *key_index_dev, ksort_stream_t stream);
+
 /* ksort_partition_out without any allocation. The paper has no counterpart: it is a
  * library form for callers that must not allocate device memory. Examples are a
  * process that has given all free HBM to its own pool allocator (cudaMalloc would

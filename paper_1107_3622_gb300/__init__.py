@@ -18,7 +18,8 @@ import threading
 
 __all__ = [
     "KSortError", "F32", "F64", "U32", "load", "library_path",
-    "ksort_partition", "ksort_partition_out", "ksort_partition_out_noalloc", "ksort_sort", "ksort_sort_batched",
+    "ksort_partition", "ksort_partition_out", "ksort_partition_out_noalloc",
+    "ksort_partition_exact", "partition_exact", "ksort_sort", "ksort_sort_batched",
     "ksort_reserve_workspace", "ksort_release_workspace", "ksort_get_device_error",
     "ksort_get_stats", "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
     "ksort_tile_keys", "ksort_tile_shape", "ksort_status_string", "ksort_last_cuda_error",
@@ -87,6 +88,7 @@ def load():
             "ksort_partition": (i32, [i32, vp, i64, vp, vp]),
             "ksort_partition_out": (i32, [i32, vp, vp, i64, vp, vp]),
             "ksort_partition_out_noalloc": (i32, [i32, vp, vp, i64, vp, vp]),
+            "ksort_partition_exact": (i32, [i32, vp, vp, i64, vp, vp]),
             "ksort_sort": (i32, [i32, vp, i64, vp]),
             "ksort_sort_batched": (i32, [i32, vp, vp, i64, i64, vp]),
             "ksort_reserve_workspace": (i32, [i32, i64, i64, vp]),
@@ -176,6 +178,12 @@ def ksort_partition_out_noalloc(dtype: int, src, dst, n: int, key_index, stream=
     (n <= KSORT_NOALLOC_MAX_KEYS). A device-side error shows as a negative key index."""
     _check(load().ksort_partition_out_noalloc(dtype, _ptr(src), _ptr(dst), n, _ptr(key_index),
                                               _stream(stream)), "ksort_partition_out_noalloc")
+
+
+def ksort_partition_exact(dtype: int, src, dst, n: int, key_index, stream=None):
+    """Steps 1-4 into ``dst`` in the paper's own element order (the hole scheme's layout)."""
+    _check(load().ksort_partition_exact(dtype, _ptr(src), _ptr(dst), n, _ptr(key_index),
+                                        _stream(stream)), "ksort_partition_exact")
 
 
 def ksort_sort(dtype: int, keys, n: int, stream=None):
@@ -276,6 +284,18 @@ def partition_out(src, dst, dtype=None, stream=None):
     idx = torch.empty(1, dtype=torch.int64, device=src.device)
     ksort_partition_out(code, src, dst, src.numel(), idx, stream)
     return idx
+
+
+def partition_exact(src, dst, dtype=None, stream=None) -> int:
+    """Steps 1-4 from ``src`` into ``dst`` with the paper's element order; returns the
+    key's final index."""
+    import torch
+    code = dtype_code(src, dtype)
+    if dst.dtype != src.dtype or dst.numel() != src.numel():
+        raise ValueError("dst must match src in dtype and size")
+    idx = torch.empty(1, dtype=torch.int64, device=src.device)
+    ksort_partition_exact(code, src, dst, src.numel(), idx, stream)
+    return int(idx.item())
 
 
 def sort_(t, dtype=None, stream=None):

@@ -45,13 +45,16 @@ struct Ops {
   long long (*tile_count)(int, const void *, long long, long long);
   cudaError_t (*part_occupancy)(int, int *);
   cudaError_t (*partition)(const SortParams &, int, int, cudaStream_t);
+  size_t (*exact_work_bytes)(long long);
+  cudaError_t (*exact)(const void *, void *, long long, long long *, void *, cudaStream_t);
 };
 
 template <typename K>
 Ops ops_for() {
   return Ops{&Launcher<K>::info,       &Launcher<K>::small_smem_bytes, &Launcher<K>::occupancy,
              &Launcher<K>::seed,       &Launcher<K>::tiles,            &Launcher<K>::smalls,
-             &Launcher<K>::tile_count, &Launcher<K>::part_occupancy,   &Launcher<K>::partition};
+             &Launcher<K>::tile_count, &Launcher<K>::part_occupancy,   &Launcher<K>::partition,
+             &Launcher<K>::exact_work_bytes, &Launcher<K>::exact};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -331,6 +334,37 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   return KSORT_OK;
 }
 
+ksort_status_t partition_exact_impl(ksort_dtype_t dt, const void *in, void *out, int64_t n,
+                                    int64_t *key_index, cudaStream_t s) {
+  if (!dtype_ok(dt)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (n < 1 || n > kMaxItemKeys) return KSORT_ERR_INVALID_ARG;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  const size_t kb = key_bytes(dt);
+  if ((st = check_device_ptr(in, kb, dev)) != KSORT_OK) return st;
+  if ((st = check_device_ptr(out, kb, dev)) != KSORT_OK) return st;
+  if ((st = check_device_ptr(key_index, 8, dev)) != KSORT_OK) return st;
+  {
+    const char *a = static_cast<const char *>(in), *b = static_cast<const char *>(out);
+    if (a < b + n * kb && b < a + n * kb) return KSORT_ERR_INVALID_ARG;
+  }
+  if (n == 1) {
+    KS_CUDA(cudaMemsetAsync(key_index, 0, sizeof(int64_t), s));
+    KS_CUDA(cudaMemcpyAsync(out, in, kb, cudaMemcpyDeviceToDevice, s));
+    return KSORT_OK;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Tuning tu = g_tuning[dt];
+  Need need = need_for(dt, 1, 1, tu.variant);
+  need.item_cap = 64;
+  need.scratch_bytes = ops(dt).exact_work_bytes(n);
+  Workspace *ws = nullptr;
+  if ((st = get_workspace(dev, s, need, &ws)) != KSORT_OK) return st;
+  KS_CUDA(ops(dt).exact(in, out, n, reinterpret_cast<long long *>(key_index), ws->scratch, s));
+  return KSORT_OK;
+}
+
 ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, int64_t num_arrays,
                          int64_t total, cudaStream_t s) {
   if (!dtype_ok(dt)) return KSORT_ERR_UNSUPPORTED_DTYPE;
@@ -519,6 +553,11 @@ ksort_status_t ksort_partition_out_noalloc(ksort_dtype_t dtype, const void *in_d
                                            int64_t n, int64_t *key_index_dev,
                                            ksort_stream_t stream) {
   return partition_noalloc_impl(dtype, in_dev, out_dev, n, key_index_dev, (cudaStream_t)stream);
+}
+
+ksort_status_t ksort_partition_exact(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
+                                     int64_t n, int64_t *key_index_dev, ksort_stream_t stream) {
+  return partition_exact_impl(dtype, in_dev, out_dev, n, key_index_dev, (cudaStream_t)stream);
 }
 
 ksort_status_t ksort_sort(ksort_dtype_t dtype, void *keys_dev, int64_t n, ksort_stream_t stream) {

@@ -2185,6 +2185,224 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) part_kernel(SortParam
   }
 }
 
+// ----------------------------------------------------------------------------- exact
+// Steps 1-4 with the paper's own element order: the hole scheme of Step 3 (a front scan
+// that moves each element below the key one place left and sends each element >= the key
+// to the back hole, and a back scan that leaves elements >= the key in place and sends
+// each element below the key to the front hole) has a closed form. Number the elements
+// after the key 0..m-1; let F_t be the t-th element >= key from the front and B_t the
+// t-th element < key from the back (0-based t), L = #{< key}, and T the number of t with
+// F_t before B_t (a prefix of t: F_t is before B_t exactly when at least t+1 elements
+// < key follow it). Then, as indices of the sub-array (the key was at 0):
+//   the key goes to L;
+//   B_t, t < T, goes to the index of F_t; every other element < key at k goes to k;
+//   F_0 goes to L + 1 (Step 4's temp);
+//   F_t, 1 <= t < T, goes to the index of B_{t-1} plus 1, and so does F_T when T >= 1 and
+//   F_T comes before B_{T-1}; every other element >= key at k stays at k + 1.
+// Four passes: tile counts, their scan (one CTA), per-element ranks (recording where each
+// F_t and B_t is, and counting the pairs), and the placement.
+constexpr int kExactThreads = 256, kExactIpt = 4, kExactTile = kExactThreads * kExactIpt;
+
+template <typename K>
+__global__ void __launch_bounds__(kExactThreads) exact_count_kernel(const K *a, long long m,
+                                                                    unsigned *tile_less) {
+  const K key = a[0];
+  const K *b = a + 1;
+  const long long g = blockIdx.x;
+  const long long base = g * kExactTile + (long long)threadIdx.x * kExactIpt;
+  unsigned c = 0;
+#pragma unroll
+  for (int i = 0; i < kExactIpt; ++i)
+    if (base + i < m) c += goes_left(key, b[base + i]) ? 1u : 0u;
+  c = __reduce_add_sync(kFull, c);
+  __shared__ unsigned ws[kExactThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int w = 0; w < kExactThreads / 32; ++w) tot += ws[w];
+    tile_less[g] = tot;
+  }
+}
+
+// One CTA: ge_before[g] = elements >= key in tiles before g, less_after[g] = elements < key
+// in tiles after g; *L_out = all elements < key.
+template <int NT>
+__global__ void __launch_bounds__(NT) exact_scan_kernel(const unsigned *tile_less,
+                                                          long long tiles, long long m,
+                                                          unsigned long long *ge_before,
+                                                          unsigned long long *less_after,
+                                                          unsigned long long *L_out) {
+  __shared__ unsigned long long wsum[32], carry_ge, carry_less;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    carry_ge = 0;
+    carry_less = 0;
+  }
+  __syncthreads();
+  // forward: ge counts
+  for (long long c0 = 0; c0 < tiles; c0 += NT) {
+    const long long g = c0 + tid;
+    unsigned long long v = 0;
+    if (g < tiles) {
+      const long long sz = (g == tiles - 1) ? m - g * kExactTile : kExactTile;
+      v = (unsigned long long)sz - tile_less[g];
+    }
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    unsigned long long wb = 0;
+    for (int i = 0; i < w; ++i) wb += wsum[i];
+    if (g < tiles) ge_before[g] = carry_ge + wb + x - v;
+    __syncthreads();
+    if (tid == NT - 1) carry_ge += wb + x;
+    __syncthreads();
+  }
+  // backward: less counts after each tile
+  for (long long c0 = 0; c0 < tiles; c0 += NT) {
+    const long long g = tiles - 1 - (c0 + tid);  // tid 0 takes the last tile
+    const unsigned long long v = g >= 0 ? tile_less[g] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long u = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    unsigned long long wb = 0;
+    for (int i = 0; i < w; ++i) wb += wsum[i];
+    if (g >= 0) less_after[g] = carry_less + wb + x - v;
+    __syncthreads();
+    if (tid == NT - 1) carry_less += wb + x;
+    __syncthreads();
+  }
+  if (tid == 0) *L_out = carry_less;
+}
+
+// Ranks inside a tile: element k's exclusive ge count and inclusive less count (thread
+// i holds elements base + i*IPT ... + IPT - 1).
+struct ExactRanks {
+  unsigned ge_excl[kExactIpt], less_incl[kExactIpt];
+  unsigned tile_less;
+};
+template <typename K>
+__device__ __forceinline__ void exact_ranks(const K *b, long long m, K key, long long base,
+                                            bool (&lf)[kExactIpt], bool (&valid)[kExactIpt],
+                                            ExactRanks &r) {
+  __shared__ unsigned wl[kExactThreads / 32], wg[kExactThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned nl = 0, ng = 0;
+#pragma unroll
+  for (int i = 0; i < kExactIpt; ++i) {
+    valid[i] = base + i < m;
+    lf[i] = valid[i] && goes_left(key, b[base + i]);
+    nl += lf[i] ? 1u : 0u;
+    ng += (valid[i] && !lf[i]) ? 1u : 0u;
+  }
+  unsigned xl = nl, xg = ng;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned ul = __shfl_up_sync(kFull, xl, o), ug = __shfl_up_sync(kFull, xg, o);
+    if (lane >= o) {
+      xl += ul;
+      xg += ug;
+    }
+  }
+  if (lane == 31) {
+    wl[w] = xl;
+    wg[w] = xg;
+  }
+  __syncthreads();
+  unsigned bl = 0, bg = 0, tl = 0;
+  for (int i = 0; i < kExactThreads / 32; ++i) {
+    if (i < w) {
+      bl += wl[i];
+      bg += wg[i];
+    }
+    tl += wl[i];
+  }
+  unsigned cl = bl + xl - nl, cg = bg + xg - ng;  // before this thread
+#pragma unroll
+  for (int i = 0; i < kExactIpt; ++i) {
+    r.ge_excl[i] = cg;
+    cl += lf[i] ? 1u : 0u;
+    r.less_incl[i] = cl;
+    cg += (valid[i] && !lf[i]) ? 1u : 0u;
+  }
+  r.tile_less = tl;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kExactThreads) exact_rank_kernel(
+    const K *a, long long m, const unsigned long long *ge_before,
+    const unsigned long long *less_after, int *Fpos, int *Bpos, unsigned long long *T_out) {
+  const K key = a[0];
+  const K *b = a + 1;
+  const long long g = blockIdx.x;
+  const long long base = g * kExactTile + (long long)threadIdx.x * kExactIpt;
+  bool lf[kExactIpt], valid[kExactIpt];
+  ExactRanks r;
+  exact_ranks(b, m, key, base, lf, valid, r);
+  unsigned pairs = 0;
+#pragma unroll
+  for (int i = 0; i < kExactIpt; ++i) {
+    if (!valid[i]) continue;
+    const long long k = base + i;
+    const unsigned long long after = less_after[g] + (r.tile_less - r.less_incl[i]);
+    if (lf[i]) {
+      Bpos[after] = (int)k;  // B_t with t = #{< key after k}
+    } else {
+      const unsigned long long t = ge_before[g] + r.ge_excl[i];
+      Fpos[t] = (int)k;  // F_t
+      pairs += after >= t + 1 ? 1u : 0u;  // F_t before B_t
+    }
+  }
+  pairs = __reduce_add_sync(kFull, pairs);
+  if ((threadIdx.x & 31) == 0 && pairs) atomicAdd(T_out, (unsigned long long)pairs);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kExactThreads) exact_place_kernel(
+    const K *a, long long m, const unsigned long long *ge_before,
+    const unsigned long long *less_after, const int *Fpos, const int *Bpos,
+    const unsigned long long *T_in, const unsigned long long *L_in, K *out, long long *key_index) {
+  const K key = a[0];
+  const K *b = a + 1;
+  const long long g = blockIdx.x;
+  const long long base = g * kExactTile + (long long)threadIdx.x * kExactIpt;
+  const unsigned long long T = *T_in, L = *L_in;
+  bool lf[kExactIpt], valid[kExactIpt];
+  ExactRanks r;
+  exact_ranks(b, m, key, base, lf, valid, r);
+#pragma unroll
+  for (int i = 0; i < kExactIpt; ++i) {
+    if (!valid[i]) continue;
+    const long long k = base + i;
+    long long dest;
+    if (lf[i]) {
+      const unsigned long long t = less_after[g] + (r.tile_less - r.less_incl[i]);
+      dest = t < T ? (long long)Fpos[t] : k;
+    } else {
+      const unsigned long long t = ge_before[g] + r.ge_excl[i];
+      if (t == 0) dest = (long long)L + 1;
+      else if (t < T) dest = (long long)Bpos[t - 1] + 1;
+      else if (t == T && k < (long long)Bpos[T - 1]) dest = (long long)Bpos[T - 1] + 1;
+      else dest = k + 1;
+    }
+    out[dest] = b[k];
+  }
+  if (g == 0 && threadIdx.x == 0) {
+    out[L] = key;  // Step 4
+    if (key_index) *key_index = (long long)L;
+  }
+}
+
 // Phase 2: every small sub-array, claimed from the complete list, is loaded into shared
 // memory and finished by smem_ksort. Dynamic shared memory: A and B (cutoff keys
 // each), then the per-warp leaf lists.

@@ -121,6 +121,11 @@ struct Launcher {
   // single partitions: part_kernel with CTA shape `shape` (0 .. kTileShapes - 1)
   static cudaError_t part_occupancy(int shape, int *ctas);
   static cudaError_t partition(const SortParams &p, int shape, int grid, cudaStream_t s);
+  // Steps 1-4 in the paper's element order (exact layout), n >= 2; `work` holds
+  // exact_work_bytes(n) bytes of device scratch.
+  static size_t exact_work_bytes(long long n);
+  static cudaError_t exact(const void *in, void *out, long long n, long long *key_index,
+                           void *work, cudaStream_t s);
 };
 
 }  // namespace ksort

@@ -173,6 +173,61 @@ cudaError_t Launcher<K>::partition(const SortParams &p, int shape, int grid, cud
   });
 }
 
+// Scratch of the exact-layout partition: [tile counts][ge before][less after][T][L]
+// [F positions][B positions], each part 16-byte aligned.
+struct ExactWork {
+  unsigned *tile_less;
+  unsigned long long *ge_before, *less_after, *T, *L;
+  int *Fpos, *Bpos;
+};
+inline size_t exact_layout(long long n, char *base, ExactWork *w) {
+  const long long m = n - 1;
+  const long long tiles = (m + dev::kExactTile - 1) / dev::kExactTile;
+  auto up = [](size_t x) { return (x + 15) / 16 * 16; };
+  size_t off = 0;
+  const size_t o_tl = off; off = up(off + tiles * sizeof(unsigned));
+  const size_t o_gb = off; off = up(off + tiles * sizeof(unsigned long long));
+  const size_t o_la = off; off = up(off + tiles * sizeof(unsigned long long));
+  const size_t o_T = off;  off = up(off + sizeof(unsigned long long));
+  const size_t o_L = off;  off = up(off + sizeof(unsigned long long));
+  const size_t o_F = off;  off = up(off + m * sizeof(int));
+  const size_t o_B = off;  off = up(off + m * sizeof(int));
+  if (w) {
+    w->tile_less = reinterpret_cast<unsigned *>(base + o_tl);
+    w->ge_before = reinterpret_cast<unsigned long long *>(base + o_gb);
+    w->less_after = reinterpret_cast<unsigned long long *>(base + o_la);
+    w->T = reinterpret_cast<unsigned long long *>(base + o_T);
+    w->L = reinterpret_cast<unsigned long long *>(base + o_L);
+    w->Fpos = reinterpret_cast<int *>(base + o_F);
+    w->Bpos = reinterpret_cast<int *>(base + o_B);
+  }
+  return off;
+}
+
+template <typename K>
+size_t Launcher<K>::exact_work_bytes(long long n) {
+  return exact_layout(n, nullptr, nullptr);
+}
+
+template <typename K>
+cudaError_t Launcher<K>::exact(const void *in, void *out, long long n, long long *key_index,
+                               void *work, cudaStream_t s) {
+  const long long m = n - 1;
+  const long long tiles = (m + dev::kExactTile - 1) / dev::kExactTile;
+  ExactWork w{};
+  exact_layout(n, static_cast<char *>(work), &w);
+  const K *a = static_cast<const K *>(in);
+  cudaError_t e = cudaMemsetAsync(w.T, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  dev::exact_count_kernel<K><<<(unsigned)tiles, dev::kExactThreads, 0, s>>>(a, m, w.tile_less);
+  dev::exact_scan_kernel<1024><<<1, 1024, 0, s>>>(w.tile_less, tiles, m, w.ge_before, w.less_after, w.L);
+  dev::exact_rank_kernel<K><<<(unsigned)tiles, dev::kExactThreads, 0, s>>>(
+      a, m, w.ge_before, w.less_after, w.Fpos, w.Bpos, w.T);
+  dev::exact_place_kernel<K><<<(unsigned)tiles, dev::kExactThreads, 0, s>>>(
+      a, m, w.ge_before, w.less_after, w.Fpos, w.Bpos, w.T, w.L, static_cast<K *>(out), key_index);
+  return cudaGetLastError();
+}
+
 template <typename K>
 cudaError_t Launcher<K>::smalls(const SortParams &p, int grid, cudaStream_t s) {
   auto sk = dev::small_kernel<K>;
