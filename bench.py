@@ -77,6 +77,8 @@ def parse_args(argv=None):
     ap.add_argument("--sweep", action="store_true",
                     help="instead of the headline line: the Table 1 size sweep (float32 and "
                          "float64, 20 repetitions per size) as one JSON line")
+    ap.add_argument("--sweep-pattern", default="uniform", choices=("uniform", "quantized15"),
+                    help="inputs of --sweep: U[0,1], or U[0,1] on 2**15 levels")
     ap.add_argument("--sweep-oracle-reps", type=int, default=2,
                     help="oracle repetitions per size in --sweep (0 skips the oracle)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -671,6 +673,7 @@ def run_sweep(args):
     peak, every output checked sorted; the oracle's mean time on a few of the same arrays."""
     import torch
     import paper_1107_3622_gb300 as ks
+    from paper_1107_3622_gb300 import statbound
     import oracle
     torch.cuda.set_device(0)
     ks.load()
@@ -685,7 +688,11 @@ def run_sweep(args):
             cfg = 1 if name == "f32" else 2
             ms, algo = [], []
             for r in range(reps):
-                keys = gen.uniform_torch(name, gen.seed_for(cfg, si, r), n, device="cuda")
+                if args.sweep_pattern == "uniform":
+                    keys = gen.uniform_torch(name, gen.seed_for(cfg, si, r), n, device="cuda")
+                else:
+                    keys = torch.from_numpy(
+                        gen.make(args.sweep_pattern, name, n, gen.seed_for(cfg, si, r))).cuda()
                 if r == 0:  # warm-up on the first array
                     w = keys.clone()
                     ks.ksort_sort(code, w, n)
@@ -713,7 +720,7 @@ def run_sweep(args):
             if args.sweep_oracle_reps > 0:
                 t = []
                 for r in range(args.sweep_oracle_reps):
-                    a = gen.make("uniform", name, n, gen.seed_for(cfg, si, r))
+                    a = gen.make(args.sweep_pattern, name, n, gen.seed_for(cfg, si, r))
                     t0 = time.perf_counter()
                     oracle.sort(a)
                     t.append(time.perf_counter() - t0)
@@ -721,7 +728,16 @@ def run_sweep(args):
                 row["oracle_reps"] = len(t)
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
-    return {"sweep": "Table 1 sizes, ksort_sort, f32 and f64 U[0,1]", "peak": peak,
+    fits = {}
+    for name in ("f32", "f64"):
+        rs = [r for r in rows if r["dtype"] == name]
+        ns = [r["n"] for r in rs]
+        fits[name] = {"gpu_ms": statbound.summary(statbound.fit(ns, [r["mean_ms"] for r in rs]))}
+        if args.sweep_oracle_reps > 0:
+            fits[name]["oracle_s"] = statbound.summary(
+                statbound.fit(ns, [r["oracle_mean_s"] for r in rs]))
+    return {"sweep": f"Table 1 sizes, ksort_sort, f32 and f64, {args.sweep_pattern} inputs",
+            "model_fit": fits, "peak": peak,
             "peak_source": f"{peak_src} hbm_gbs", "tuning": {"f32": ks.ksort_get_tuning(ks.F32),
                                                              "f64": ks.ksort_get_tuning(ks.F64)},
             "oracle": "C oracle, 1 thread, gcc -O2", "rows": rows}

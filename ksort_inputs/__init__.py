@@ -16,6 +16,7 @@ Value maps (all exact, no rounding):
     float64 U[0,1)  = (x >> 11) * 2**-53
     uint32 uniform  = x >> 32
     16 distinct     = x >> 60                 (values 0..15, as uint32 or float32)
+    15-bit U[0,1)   = (x >> 49) * 2**-15      (32768 levels: a duplicate-heavy U[0,1])
 
 Seeds: ``seed_for(config, size_idx, rep) = 0x11073622 ^ (config << 48) ^ (size_idx << 32) ^ rep``.
 
@@ -80,6 +81,15 @@ def distinct16_f32(seed: int, n: int) -> np.ndarray:
     return distinct16_u32(seed, n).astype(np.float32)
 
 
+def quantized15(dtype: str, seed: int, n: int) -> np.ndarray:
+    """U[0,1) on a grid of 2**15 levels, (x >> 49) * 2**-15: each value repeats about
+    n / 32768 times (uint32: the level index itself)."""
+    q = splitmix64(seed, n) >> np.uint64(49)
+    if dtype == "u32":
+        return q.astype(np.uint32)
+    return (q.astype(np.float64) * (2.0 ** -15)).astype(NP_DTYPE[dtype])
+
+
 def organ_pipe(n: int, dtype) -> np.ndarray:
     """a[i] = min(i, n-1-i): rises then falls (exact in float32 for n < 2**25)."""
     i = np.arange(n, dtype=np.int64)
@@ -91,7 +101,8 @@ NP_DTYPE = {"f32": np.float32, "f64": np.float64, "u32": np.uint32}
 
 
 def make(pattern: str, dtype: str, n: int, seed: int) -> np.ndarray:
-    """One input array. ``pattern`` in {uniform, sorted, reverse, distinct16, organ_pipe}.
+    """One input array. ``pattern`` in {uniform, sorted, reverse, distinct16, organ_pipe,
+    quantized15}.
 
     ``sorted``/``reverse`` are the uniform draw sorted ascending / descending, as the
     stress configuration describes (already-sorted and reverse-sorted inputs).
@@ -106,6 +117,8 @@ def make(pattern: str, dtype: str, n: int, seed: int) -> np.ndarray:
         return distinct16_u32(seed, n).astype(NP_DTYPE[dtype])
     if pattern == "organ_pipe":
         return organ_pipe(n, NP_DTYPE[dtype])
+    if pattern == "quantized15":
+        return quantized15(dtype, seed, n)
     raise ValueError(f"unknown pattern {pattern!r}")
 
 

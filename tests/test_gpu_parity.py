@@ -118,7 +118,8 @@ def test_sort_uniform(ref, ks, dtype, n):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "u32"])
-@pytest.mark.parametrize("pattern", ["sorted", "reverse", "distinct16", "organ_pipe"])
+@pytest.mark.parametrize("pattern", ["sorted", "reverse", "distinct16", "organ_pipe",
+                                     "quantized15"])
 @pytest.mark.parametrize("n", [20_000, 50_000])
 def test_sort_stress(ref, ks, dtype, pattern, n):
     """Input-structure stress at oracle-feasible sizes: the paper's worst cases for the
@@ -163,3 +164,11 @@ def test_stats_account_for_every_key(ks):
     assert st["large_keys"] >= n and st["small_keys"] <= n
     assert st["tiles"] >= st["large_items"] >= 1
     assert st["items_pushed"] == st["large_items"] + st["small_items"]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sort_duplicate_heavy(ref, ks, dtype):
+    """U[0,1] on 2**15 levels (each value about n / 32768 times): long runs of keys equal
+    to their sub-array's key, which Step 3 sends right one partition at a time."""
+    a = gen.make("quantized15", dtype, 1_000_000, gen.seed_for(8, 0, 0))
+    assert gpu_sort(ks, a).tobytes() == oracle_sort(ref, a).tobytes()

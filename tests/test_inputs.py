@@ -44,6 +44,11 @@ def test_patterns():
     assert np.all(np.diff(r.astype(np.int64)) <= 0)
     o = gen.make("organ_pipe", "f32", 7, 0)
     assert o.tolist() == [0, 1, 2, 3, 2, 1, 0]
+    q = gen.make("quantized15", "f32", 200_000, 3)
+    assert q.min() >= 0 and q.max() < 1 and len(np.unique(q)) <= 32768
+    assert np.all(q * 32768 == np.floor(q * 32768))        # on the 2**-15 grid
+    u = gen.uniform_f64(3, 200_000)                          # the same stream, truncated
+    assert np.array_equal(q, (np.floor(u * 32768) / 32768).astype(np.float32))
 
 
 def test_batched_lengths():
