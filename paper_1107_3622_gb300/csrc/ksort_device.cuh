@@ -86,6 +86,25 @@ template <> struct Vec<double> { using T = double2; static constexpr int N = 2; 
 template <typename K>
 __device__ __forceinline__ bool goes_left(K key, K x) { return !(key <= x); }
 
+// float64 keys are classified on the integer pipes: this GPU issues FP64 instructions,
+// compares included, at a small fraction of the FP32 and integer rates. The IEEE-754
+// order of two doubles that are not NaN is the unsigned order of
+//     sign ? ~bits : bits | 2^63
+// once -0 is read as +0, and `key <= x` is false when either operand is NaN, so the
+// result is the same as the floating-point compare for every pair of inputs.
+__device__ __forceinline__ unsigned long long f64_order(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b << 1) == 0ull) b = 0ull;  // -0 == +0
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ bool f64_nan(double v) {
+  return ((unsigned long long)__double_as_longlong(v) << 1) > 0xffe0000000000000ull;
+}
+template <>
+__device__ __forceinline__ bool goes_left<double>(double key, double x) {
+  return f64_nan(key) | f64_nan(x) | (f64_order(key) > f64_order(x));
+}
+
 template <typename K>
 __device__ __forceinline__ unsigned long long key_bits(K k) {
   unsigned long long b = 0;

@@ -172,3 +172,49 @@ def test_sort_duplicate_heavy(ref, ks, dtype):
     to their sub-array's key, which Step 3 sends right one partition at a time."""
     a = gen.make("quantized15", dtype, 1_000_000, gen.seed_for(8, 0, 0))
     assert gpu_sort(ks, a).tobytes() == oracle_sort(ref, a).tobytes()
+
+
+def _f64_specials(seed, n, with_nan):
+    """float64 keys over the whole range: both signs, subnormals, extremes, infinities,
+    +0 and -0 (and NaN when asked), mixed with normal values."""
+    rng = np.random.default_rng(seed)
+    pool = [0.0, np.inf, -np.inf, 5e-324, -5e-324, 2.2250738585072014e-308,
+            -2.2250738585072014e-308, 1.7976931348623157e308, -1.7976931348623157e308,
+            1.0, -1.0, 0.5]
+    if with_nan:
+        pool += [np.nan, -0.0]
+    a = rng.standard_normal(n) * 10.0 ** rng.integers(-300, 300, n)
+    pick = rng.random(n) < 0.3
+    a[pick] = rng.choice(np.array(pool), int(pick.sum()))
+    return a
+
+
+@pytest.mark.parametrize("n", [2, 31, 5000, 70_001, 1_000_003])
+def test_f64_special_values(ref, ks, n):
+    """float64 classification (done on integer pipes) equals the IEEE compare of the
+    oracle for every class of double: sorts bit-identical without NaN and -0 (where the
+    sorted array is unique), and partitions with NaN and -0 give the oracle's key index
+    and sides, for every choice of key class."""
+    a = _f64_specials(gen.seed_for(8, 1, n), n, with_nan=False)
+    assert gpu_sort(ks, a).tobytes() == oracle_sort(ref, a).tobytes()
+    import torch
+    bits = lambda v: np.sort(v.view(np.uint64)).tobytes()  # noqa: E731 (multiset of patterns)
+    pool = [np.nan, -0.0, 0.0, np.inf, -np.inf, 5e-324, -1.0]
+    for j, key in enumerate(pool):
+        a = _f64_specials(gen.seed_for(8, 2 + j, n), n, with_nan=True)
+        a[0] = key
+        want = a.copy()
+        ri, *_ = ref.partition(want)
+        for out_of_place in (False, True):
+            t = to_dev(a)
+            if out_of_place:
+                dst = torch.empty_like(t)
+                i = int(ks.partition_out(t, dst).item())
+                got = to_host(dst)
+            else:
+                i = ks.partition_(t)
+                got = to_host(t)
+            assert ks.ksort_get_device_error() == 0
+            assert i == ri, (key, out_of_place)
+            assert got[i:i + 1].tobytes() == a[:1].tobytes()
+            assert bits(got[:i]) == bits(want[:ri]) and bits(got[i + 1:]) == bits(want[ri + 1:])
