@@ -255,7 +255,8 @@ def device_source_hash():
     return h.hexdigest()[:16]
 
 
-TILE_KERNELS = {0: "tile_kernel", 1: "tile_pipe_kernel", 2: "tile_ws_kernel"}
+TILE_KERNELS = {0: "tile_kernel", 1: "tile_pipe_kernel", 2: "tile_ws_kernel",
+                3: "wave_scatter_kernel"}
 
 
 def tile_kernel_name(ks, dtype_code: int) -> str:
@@ -501,7 +502,8 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     assert float(o[i]) == float(ins[0][0])
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
-                        tile_shape=saved["tile_shape"])
+                        tile_shape=saved["tile_shape"],
+                        wave_levels=saved.get("wave_levels", -1))
     return {"kernel": f"ksort_partition_out: {kname} <float>, one launch",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
@@ -598,7 +600,8 @@ def run_batched(ks, args):
     # per-array loop, under the single-array tuning
     ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
                         ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
-                        tile_shape=sort_tuning["tile_shape"])
+                        tile_shape=sort_tuning["tile_shape"],
+                        wave_levels=sort_tuning.get("wave_levels", -1))
     bounds = [(int(off[r]), int(off[r + 1])) for r in range(len(lengths))]
     keys.copy_(pristine)
     for b, e in bounds[:16]:
@@ -633,7 +636,8 @@ def run_serving(ks, count: int, tuning: dict):
     # serving batches take the batched form's tuning, for both 4-byte key types
     for code in (ks.F32, ks.U32):
         ks.ksort_set_tuning(code, cutoff=tuning["cutoff"], ctas_per_sm=tuning["ctas_per_sm"] or -1,
-                            tile_shape=tuning["tile_shape"])
+                            tile_shape=tuning["tile_shape"],
+                            wave_levels=tuning.get("wave_levels", -1))
     cap = serving.measure_capacity()
     rate = 0.8 * cap / serving.mean_length()
     reqs = serving.poisson_requests(count, rate)
@@ -659,7 +663,7 @@ def run_serving(ks, count: int, tuning: dict):
                 "alone_vs_mix_identical": mismatches == 0, "checked": len(reqs),
                 "mismatches": mismatches, "check_s": round(time.perf_counter() - t0, 2),
                 "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning[k] for k in
-                                                           ("cutoff", "ctas_per_sm", "tile_shape")},
+                                                           ("cutoff", "ctas_per_sm", "tile_shape", "wave_levels")},
                 "latency": "arrival -> completion event of the request's batch"})
     del pools
     torch.cuda.empty_cache()

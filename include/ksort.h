@@ -174,15 +174,19 @@ KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *o
  *   ctas_per_sm:   shared-memory finisher CTAs per SM (capped by occupancy);
  *                  -1 = as many as fit (the default);
  *   spin_limit_ms: time limit of every device-side wait (1 .. 600000);
- *   tile_shape:    form of the partition passes, 1 .. 9 (1 = default); see
+ *   tile_shape:    form of the partition passes, 1 .. 12 (1 = default); see
  *                  ksort_tile_shape(). Changing it may grow a stream's workspace on
  *                  the next call, so reserve again before capturing a graph.
+ *   wave_levels:   forms 10 .. 12 only: recursion levels run as level-synchronous
+ *                  passes before the work queue takes over (1 .. 64); -1 = automatic
+ *                  (about log2 of the mean array length over the cutoff, plus 2).
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
     int32_t ctas_per_sm;
     int32_t spin_limit_ms;
     int32_t tile_shape;
+    int32_t wave_levels;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);
@@ -192,15 +196,20 @@ KSORT_API int32_t ksort_max_cutoff(ksort_dtype_t dtype);
  * tuning (threads x keys per thread of its tile shape). */
 KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
 
-/* Form `shape` (1 .. 9) of the partition passes for `dtype`: CTAs of *threads threads,
+/* Form `shape` (1 .. 12) of the partition passes for `dtype`: CTAs of *threads threads,
  * whose tile-holding threads each hold *keys_per_thread keys (a multiple of the 128-bit
- * vector). Three CTA shapes come in three kinds (*form):
- *   0 (shapes 1-3): every thread loads its keys of a tile straight into registers;
- *   1 (shapes 4-6): the next tile is staged into shared memory by a bulk copy while the
- *                   current one is finished;
- *   2 (shapes 7-9): warp roles, with one warp loading tiles by bulk copies, one warp
- *                   running look-backs and completions, and the rest (threads - 64)
- *                   counting, scattering and writing, so consecutive tiles overlap. */
+ * vector). Three CTA shapes come in four kinds (*form):
+ *   0 (shapes 1-3):   every thread loads its keys of a tile straight into registers;
+ *   1 (shapes 4-6):   the next tile is staged into shared memory by a bulk copy while
+ *                     the current one is finished;
+ *   2 (shapes 7-9):   warp roles, with one warp loading tiles by bulk copies, one warp
+ *                     running look-backs and completions, and the rest (threads - 64)
+ *                     counting, scattering and writing, so consecutive tiles overlap;
+ *   3 (shapes 10-12): the upper recursion levels (Steps 5-6) run level by level: all
+ *                     sub-arrays of one depth are partitioned by two launches, one
+ *                     counting and one moving keys, over equal spans of their keys per
+ *                     CTA, with no waits between CTAs; the remaining levels then run as
+ *                     form 0. Single partitions (ksort_partition*) use the CTA shape only. */
 KSORT_API ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
                                           int32_t *keys_per_thread, int32_t *form);
 

@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("spin_limit_ms", ctypes.c_int32), ("tile_shape", ctypes.c_int32)]
+                ("spin_limit_ms", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -216,9 +217,10 @@ def ksort_get_stats(stream=None) -> dict:
 
 
 def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0,
-                     tile_shape: int = 0):
-    """Zero arguments keep their value; ctas_per_sm=-1 restores "as many as fit"."""
-    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape)
+                     tile_shape: int = 0, wave_levels: int = 0):
+    """Zero arguments keep their value; ctas_per_sm=-1 restores "as many as fit",
+    wave_levels=-1 the automatic level count."""
+    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape, wave_levels)
     _check(load().ksort_set_tuning(dtype, ctypes.byref(t)), "ksort_set_tuning")
 
 
@@ -226,12 +228,12 @@ def ksort_get_tuning(dtype: int) -> dict:
     t = Tuning()
     _check(load().ksort_get_tuning(dtype, ctypes.byref(t)), "ksort_get_tuning")
     return {"cutoff": t.cutoff, "ctas_per_sm": t.ctas_per_sm, "spin_limit_ms": t.spin_limit_ms,
-            "tile_shape": t.tile_shape}
+            "tile_shape": t.tile_shape, "wave_levels": t.wave_levels}
 
 
 def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
     """(threads, keys per tile-holding thread, form) of partition-pass form `shape`
-    (1-based); form 0 registers, 1 staged, 2 warp roles."""
+    (1-based); form 0 registers, 1 staged, 2 warp roles, 3 level-synchronous upper levels."""
     nt, ipt, fm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().ksort_tile_shape(dtype, shape, ctypes.byref(nt), ctypes.byref(ipt),
                                    ctypes.byref(fm)), "ksort_tile_shape")

@@ -1,13 +1,14 @@
 """Autotuner of libksort: picks, for one key type and workload (a sort, a batch of sorts
 or a single partition), the form of the partition passes (kernel kind and threads x
-keys per thread), the shared-memory cutoff below which sub-arrays are finished in SMEM,
-and the finisher's CTAs per SM.
+keys per thread), the number of level-synchronous levels when that form is the wave
+form, the shared-memory cutoff below which sub-arrays are finished in SMEM, and the
+finisher's CTAs per SM.
 
 Every candidate runs the real workload through the C ABI on the current device. The
 input is restored from a pristine copy and L2 flushed before each timed run, and CUDA
 events time the call alone. The median over `reps` runs decides. The search is
-coordinate descent: tile shape, then cutoff, then finisher CTAs, repeated while
-something improves. The winner is checked for a sorted output, applied with
+coordinate descent: tile shape, then wave levels (wave forms only), then cutoff, then
+finisher CTAs, repeated while something improves. The winner is checked for a sorted output, applied with
 ksort_set_tuning, and stored in a JSON cache keyed by device, library sources, key
 type and workload, so later processes can apply it without searching.
 """
@@ -28,7 +29,10 @@ from . import F32, F64, U32, _HERE, ksort_get_device_error, ksort_get_tuning, \
 
 _NAMES = {F32: "f32", F64: "f64", U32: "u32"}
 CUTOFFS = (1024, 2048, 4096, 8192, 16384)
-SHAPES = tuple(range(1, 10))
+SHAPES = tuple(range(1, 13))
+WAVE_SHAPES = (10, 11, 12)
+# -1: the library's automatic count; fixed counts around the depth of random inputs
+WAVE_LEVELS = (-1, 6, 9, 12, 15, 18)
 FINISHER_CTAS = (-1, 3, 2)
 _L2_FLUSH_BYTES = 256 << 20
 _lock = threading.Lock()
@@ -96,7 +100,7 @@ def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None) -> dict | None
         return None
     t = e["tuning"]
     ksort_set_tuning(dtype, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
-                     tile_shape=t["tile_shape"])
+                     tile_shape=t["tile_shape"], wave_levels=t.get("wave_levels", -1))
     return e
 
 
@@ -188,24 +192,30 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
     maxc = ksort_max_cutoff(dtype)
     cutoffs = [c for c in CUTOFFS if c <= maxc]
     best = {"tile_shape": before["tile_shape"], "cutoff": before["cutoff"],
-            "ctas_per_sm": before["ctas_per_sm"] or -1}
+            "ctas_per_sm": before["ctas_per_sm"] or -1,
+            "wave_levels": before.get("wave_levels", -1)}
     tried = {}
 
     def measure(cfg) -> float:
-        key = (cfg["tile_shape"], cfg["cutoff"], cfg["ctas_per_sm"])
+        if cfg["tile_shape"] not in WAVE_SHAPES:
+            cfg["wave_levels"] = -1  # no effect outside the wave form
+        key = (cfg["tile_shape"], cfg["cutoff"], cfg["ctas_per_sm"], cfg["wave_levels"])
         if key not in tried:
             ksort_set_tuning(dtype, cutoff=cfg["cutoff"], ctas_per_sm=cfg["ctas_per_sm"],
-                             tile_shape=cfg["tile_shape"])
+                             tile_shape=cfg["tile_shape"], wave_levels=cfg["wave_levels"])
             tried[key] = runner.time(reps)
         return tried[key]
 
     best_ms = measure(best)
-    axes = (("tile_shape", SHAPES), ("cutoff", cutoffs), ("ctas_per_sm", FINISHER_CTAS))
+    axes = (("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS), ("cutoff", cutoffs),
+            ("ctas_per_sm", FINISHER_CTAS))
     if kind == "partition":  # one part_kernel launch: only its CTA shape matters
         axes = (("tile_shape", SHAPES[:3]),)
     for _ in range(max_rounds):
         improved = False
         for name, values in axes:
+            if name == "wave_levels" and best["tile_shape"] not in WAVE_SHAPES:
+                continue
             for v in values:
                 cfg = dict(best, **{name: v})
                 ms = measure(cfg)
@@ -214,22 +224,24 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
         if not improved:
             break
     ksort_set_tuning(dtype, cutoff=best["cutoff"], ctas_per_sm=best["ctas_per_sm"],
-                     tile_shape=best["tile_shape"])
+                     tile_shape=best["tile_shape"], wave_levels=best["wave_levels"])
     if not runner.check_sorted():
         ksort_set_tuning(dtype, cutoff=before["cutoff"], ctas_per_sm=before["ctas_per_sm"] or -1,
-                         tile_shape=before["tile_shape"])
+                         tile_shape=before["tile_shape"], wave_levels=before.get("wave_levels", -1))
         raise RuntimeError("autotuned configuration produced an unsorted output")
     entry = {"workload": workload_key(kind, dtype, n, lengths), "device": device_key(),
              "library": library_hash(), "tuning": best, "ms": round(best_ms, 4),
              "keys": runner.total, "reps": reps,
              "candidates": [{"tile_shape": k[0], "cutoff": k[1], "ctas_per_sm": k[2],
-                             "ms": round(v, 4)} for k, v in sorted(tried.items())]}
+                             "wave_levels": k[3], "ms": round(v, 4)}
+                            for k, v in sorted(tried.items())]}
     if use_cache:
         _store(_full_key(kind, dtype, n, lengths), entry)
     return dict(entry, cached=False)
 
 
 def reset(dtype: int):
-    """Back to the library defaults (tile shape 1, default cutoff, all finisher CTAs)."""
+    """Back to the library defaults (tile shape 1, default cutoff, all finisher CTAs,
+    automatic wave levels)."""
     default_cutoff = {F32: 4096, F64: 2048, U32: 4096}[dtype]
-    ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1)
+    ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1, wave_levels=-1)

@@ -47,6 +47,9 @@ struct Ops {
   cudaError_t (*partition)(const SortParams &, int, int, cudaStream_t);
   size_t (*exact_work_bytes)(long long);
   cudaError_t (*exact)(const void *, void *, long long, long long *, void *, cudaStream_t);
+  cudaError_t (*wave_occupancy)(int, int *);
+  cudaError_t (*wave_level)(const SortParams &, int, int, int, bool, cudaStream_t);
+  cudaError_t (*wave_handoff)(const SortParams &, int, int, bool, cudaStream_t);
 };
 
 template <typename K>
@@ -54,7 +57,8 @@ Ops ops_for() {
   return Ops{&Launcher<K>::info,       &Launcher<K>::small_smem_bytes, &Launcher<K>::occupancy,
              &Launcher<K>::seed,       &Launcher<K>::tiles,            &Launcher<K>::smalls,
              &Launcher<K>::tile_count, &Launcher<K>::part_occupancy,   &Launcher<K>::partition,
-             &Launcher<K>::exact_work_bytes, &Launcher<K>::exact};
+             &Launcher<K>::exact_work_bytes, &Launcher<K>::exact,
+             &Launcher<K>::wave_occupancy, &Launcher<K>::wave_level, &Launcher<K>::wave_handoff};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -68,12 +72,13 @@ struct Tuning {
   int ctas_per_sm;  // 0: as many as fit
   int spin_limit_ms;
   int variant;      // tile shape of the tile passes, 0 .. kTileVariants - 1
+  int wave_levels;  // wave form: level-synchronous levels; 0: automatic
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0}, {2048, 0, 2000, 0}, {4096, 0, 2000, 0}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0}, {2048, 0, 2000, 0, 0}, {4096, 0, 2000, 0, 0}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -86,6 +91,9 @@ struct Workspace {
   ItemCtl *ictl = nullptr;
   unsigned long long *tmap = nullptr, *small_q = nullptr;
   unsigned long long item_cap = 0;
+  WaveItem *wave_items = nullptr;          // two level lists of item_cap entries
+  unsigned long long *wave_cnt = nullptr;  // 2 x kWaveMaxGrid
+  unsigned long long *wave_fin = nullptr;  // item_cap (index, key) pairs
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
   unsigned pending_error = 0;  // device error carried over from a replaced allocation
@@ -141,7 +149,8 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
     KS_CUDA(cudaFree(ws.base));
     ws.base = nullptr;
   }
-  // [Control][look-back][items][item counters][ticket map][small list][scratch keys]
+  // [Control][look-back][items][item counters][ticket map][small list][wave lists]
+  // [wave counts][late keys][scratch keys]
   size_t off = 0;
   const size_t o_ctl = off;
   off = align_up(off + sizeof(Control), 256);
@@ -155,6 +164,12 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   off = align_up(off + lb_cap * sizeof(unsigned long long), 256);
   const size_t o_sq = off;
   off = align_up(off + item_cap * sizeof(unsigned long long), 256);
+  const size_t o_wi = off;
+  off = align_up(off + 2 * item_cap * sizeof(WaveItem), 256);
+  const size_t o_wc = off;
+  off = align_up(off + 2 * kWaveMaxGrid * sizeof(unsigned long long), 256);
+  const size_t o_wf = off;
+  off = align_up(off + 2 * item_cap * sizeof(unsigned long long), 256);
   const size_t meta = off;
   const size_t o_scr = off;
   off = align_up(off + scratch_bytes + kScratchPad, 256);
@@ -180,6 +195,9 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   ws.tmap = reinterpret_cast<unsigned long long *>(b + o_tmap);
   ws.small_q = reinterpret_cast<unsigned long long *>(b + o_sq);
   ws.item_cap = item_cap;
+  ws.wave_items = reinterpret_cast<WaveItem *>(b + o_wi);
+  ws.wave_cnt = reinterpret_cast<unsigned long long *>(b + o_wc);
+  ws.wave_fin = reinterpret_cast<unsigned long long *>(b + o_wf);
   ws.scratch = b + o_scr;
   ws.scratch_bytes = scratch_bytes;
   ws.pending_error = pending;
@@ -241,6 +259,33 @@ ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g)
   return KSORT_OK;
 }
 
+std::map<std::pair<int, int>, int> g_wave_occ;  // (dtype, shape) -> level-pass CTAs per SM
+
+ksort_status_t wave_occupancy(ksort_dtype_t dt, int shape, int *occ) {
+  auto key = std::make_pair((int)dt, shape);
+  auto it = g_wave_occ.find(key);
+  if (it != g_wave_occ.end()) {
+    *occ = it->second;
+    return KSORT_OK;
+  }
+  int o = 0;
+  KS_CUDA(ops(dt).wave_occupancy(shape, &o));
+  if (o < 1) return KSORT_ERR_INTERNAL;
+  g_wave_occ[key] = o;
+  *occ = o;
+  return KSORT_OK;
+}
+
+// Wave levels when the tuning leaves it automatic: about the depth at which a random
+// array's sub-arrays fall to the cutoff (log2 of the mean array over the cutoff, plus
+// two levels for the spread of random keys); what remains goes to the work queue.
+int auto_wave_levels(long long total, long long arrays, int cutoff) {
+  const double mean = (double)total / (double)std::max<long long>(arrays, 1);
+  int w = 0;
+  for (double x = mean; x > cutoff && w < 62; x /= 2) ++w;
+  return std::max(1, w + 2);
+}
+
 std::map<std::pair<int, int>, int> g_part_occ;  // (dtype, shape) -> part_kernel CTAs per SM
 
 ksort_status_t part_occupancy(ksort_dtype_t dt, int shape, int *occ) {
@@ -274,6 +319,11 @@ SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
   p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
   p.trace = g_trace;
   p.trace_cap = g_trace_cap;
+  p.wave_items = ws.wave_items;
+  p.wave_cap = ws.item_cap;
+  p.wave_cnt = ws.wave_cnt;
+  p.wave_fin = ws.wave_fin;
+  p.wave = 0;
   return p;
 }
 
@@ -398,6 +448,25 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
   p.total = total;
   p.readable[0] = total;
   p.readable[1] = total + (long long)(kScratchPad / kb);
+  const KernelInfo kinfo = ops(dt).info(tu.variant);
+  if (kinfo.form == kWaveForm && (offsets || total > tu.cutoff)) {
+    // level-synchronous passes for the upper levels, then the work queue for the rest
+    const int shape = tu.variant % kTileShapes;
+    int wocc = 0, sms = 0;
+    if ((st = wave_occupancy(dt, shape, &wocc)) != KSORT_OK) return st;
+    if ((st = device_sms(dev, &sms)) != KSORT_OK) return st;
+    long long grid = std::min<long long>((long long)sms * wocc, kWaveMaxGrid);
+    if (!offsets) grid = std::max<long long>(1, std::min<long long>(grid, (total + kinfo.tile_keys - 1) / kinfo.tile_keys));
+    const int levels = tu.wave_levels > 0 ? tu.wave_levels
+                                          : auto_wave_levels(total, p.num_roots, tu.cutoff);
+    p.wave = 1;
+    KS_CUDA(ops(dt).seed(p, tu.variant, s));
+    for (int l = 0; l < levels; ++l) KS_CUDA(ops(dt).wave_level(p, shape, l, (int)grid, true, s));
+    KS_CUDA(ops(dt).wave_handoff(p, shape, levels, true, s));
+    KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
+    KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+    return KSORT_OK;
+  }
   KS_CUDA(ops(dt).seed(p, tu.variant, s));
   if (offsets || total > tu.cutoff) KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
   KS_CUDA(ops(dt).smalls(p, g.smalls, s));
@@ -672,12 +741,14 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->ctas_per_sm < -1 || t->spin_limit_ms < 0 || t->spin_limit_ms > 600000)
     return KSORT_ERR_INVALID_ARG;
   if (t->tile_shape < 0 || t->tile_shape > kTileVariants) return KSORT_ERR_INVALID_ARG;
+  if (t->wave_levels < -1 || t->wave_levels > 64) return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
   if (t->ctas_per_sm) g.ctas_per_sm = t->ctas_per_sm < 0 ? 0 : t->ctas_per_sm;
   if (t->spin_limit_ms) g.spin_limit_ms = t->spin_limit_ms;
   if (t->tile_shape) g.variant = t->tile_shape - 1;
+  if (t->wave_levels) g.wave_levels = t->wave_levels < 0 ? 0 : t->wave_levels;
   return KSORT_OK;
 }
 
@@ -690,6 +761,7 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->ctas_per_sm = g.ctas_per_sm;
   out->spin_limit_ms = g.spin_limit_ms;
   out->tile_shape = g.variant + 1;
+  out->wave_levels = g.wave_levels ? g.wave_levels : -1;
   return KSORT_OK;
 }
 

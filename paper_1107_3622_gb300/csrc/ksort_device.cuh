@@ -2422,6 +2422,366 @@ __global__ void __launch_bounds__(kExactThreads) exact_place_kernel(
   }
 }
 
+// ----------------------------------------------------------------------------- waves
+// Level-synchronous tile passes (the wave form) for the upper recursion levels of a
+// sort. The sub-arrays above the cutoff at one depth form the level's list; their
+// classified keys (every element but the key, Step 3) are numbered consecutively along
+// the list, the level's key space (WaveItem::koff), which is split into equal
+// contiguous spans, one per CTA, across sub-array boundaries. A level is two launches:
+//   count    each CTA counts the less keys of the first and of the last sub-array its
+//            span touches, and publishes both counts;
+//   scatter  each CTA takes the less keys before its span in its first sub-array from
+//            the counts of the CTAs before it (which hold the rest of that sub-array),
+//            then moves its keys tile by tile as tile_kernel does: less keys from the
+//            left end, >= keys from the right end. The CTA holding a sub-array's last
+//            key places its key (Step 4) and queues both sides (Steps 5-6): small sides
+//            for the SMEM finisher, large sides on the next level's list.
+// No CTA ever waits for another: the launches are ordered by the stream, and under
+// programmatic dependent launch the next launch's CTAs start as this one's leave and
+// wait (griddepcontrol.wait) until its memory is complete. After the last wave level,
+// the remaining list is handed to tile_kernel's work queue.
+// Placement of a key at an even level: the level reads buffer 0, where other CTAs of
+// the same launch may still be reading the sub-array, so the key is recorded in
+// wave_fin and written to buffer 0 by the next launch (an odd level's count, or the
+// hand-off); odd levels read buffer 1 and write the key at once.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Keys per CTA span: equal shares of the level, at least one tile each.
+__device__ __forceinline__ long long wave_span(long long keys, int grid, int tile) {
+  const long long per = (keys + grid - 1) / grid;
+  return per < tile ? (long long)tile : per;
+}
+
+template <int NW>
+struct WaveShared {
+  unsigned wl[NW], wg[NW];
+  unsigned long long red[NW];
+  int find[8];
+};
+
+// Whole CTA: the list item whose key-space range holds s (koff increases along the
+// list, items[0].koff = 0). Each round probes NT evenly spaced items, so m items take
+// ceil(log_NT m) rounds.
+template <int NT, int NW>
+__device__ __forceinline__ long long wave_find(const WaveItem *items, long long m, long long s,
+                                               WaveShared<NW> &sh) {
+  if (threadIdx.x < 8) sh.find[threadIdx.x] = 0;
+  __syncthreads();
+  long long lo = 0, hi = m;
+  for (int r = 0; hi - lo > 1 && r < 8; ++r) {
+    const long long step = (hi - lo + NT - 1) / NT;
+    const long long idx = lo + (long long)threadIdx.x * step;
+    if (threadIdx.x > 0 && idx < hi && __ldcg(&items[idx].koff) <= s)
+      atomicMax(&sh.find[r], (int)threadIdx.x);
+    __syncthreads();
+    lo += (long long)sh.find[r] * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
+// Sum over the CTA (every thread gets it); two barriers.
+template <int NW>
+__device__ __forceinline__ unsigned long long wave_sum(unsigned long long v, WaveShared<NW> &sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long t = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) t += sh.red[i];
+  __syncthreads();
+  return t;
+}
+
+// Keys [vlo, vhi) of the tile at src + lo (16-byte aligned) into registers; thread i
+// holds tile positions (v * NT + i) * VEC + l. Whole vectors inside the range move
+// with 128-bit loads, the edges one key at a time; nothing outside the range is read.
+template <typename K, int NT, int IPT>
+__device__ __forceinline__ void wave_load(const K *src, long long lo, int vlo, int vhi,
+                                          K (&x)[IPT]) {
+  constexpr int VEC = Vec<K>::N, NV = IPT / VEC;
+  using V = typename Vec<K>::T;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int k0 = (v * NT + (int)threadIdx.x) * VEC;
+    if (k0 >= vlo && k0 + VEC <= vhi) {
+      const V q = __ldcg(reinterpret_cast<const V *>(src + lo + k0));
+      if constexpr (VEC == 4) {
+        x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
+      } else {
+        x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        const int k = k0 + l;
+        x[v * VEC + l] = (k >= vlo && k < vhi) ? __ldcg(src + lo + k) : K(0);
+      }
+    }
+  }
+}
+
+// Keys recorded by the last even level go to their final index in buffer 0.
+template <typename K>
+__device__ __forceinline__ void wave_place_late_keys(const SortParams &p) {
+  unsigned long long n = __ldcg(&p.ctl->wave_fin);
+  if (n > p.wave_cap) n = p.wave_cap;  // an overflow was reported when it happened
+  K *buf0 = static_cast<K *>(p.keys);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += stride)
+    buf0[__ldcg(&p.wave_fin[2 * i])] = bits_key<K>(__ldcg(&p.wave_fin[2 * i + 1]));
+}
+
+// The level's list, its key count, and this CTA's span [*s0, *s1); false: no work.
+__device__ __forceinline__ bool wave_level_span(const SortParams &p, int level, int tile,
+                                                long long *m, long long *per, long long *s0,
+                                                long long *s1) {
+  const unsigned long long ctr = __ldcg(&p.ctl->wave_ctr[level & 1]);
+  *m = (long long)(ctr >> kWaveKeyBits);
+  const long long keys = (long long)(ctr & kWaveKeyMask);
+  if (*m == 0 || *m > (long long)p.wave_cap || __ldcg(&p.ctl->abort) != 0u) return false;
+  *per = wave_span(keys, (int)gridDim.x, tile);
+  *s0 = (long long)blockIdx.x * *per;
+  *s1 = min(*s0 + *per, keys);
+  return *s0 < keys;
+}
+
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) wave_count_kernel(SortParams p,
+                                                                             int level) {
+  constexpr int TILE = NT * IPT, VEC = Vec<K>::N, NV = IPT / VEC, NW = NT / 32;
+  __shared__ WaveShared<NW> sh;
+  grid_dep_wait();
+  grid_dep_launch();
+  Control *ctl = p.ctl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->wave_ctr[(level + 1) & 1] = 0ull;  // the next level's list starts empty
+    if ((level & 1) == 0) ctl->wave_fin = 0ull;
+  }
+  if (level & 1) wave_place_late_keys<K>(p);
+  long long m = 0, per = 0, s0 = 0, s1 = 0;
+  if (!wave_level_span(p, level, TILE, &m, &per, &s0, &s1)) return;
+  const WaveItem *items = p.wave_items + (size_t)(level & 1) * p.wave_cap;
+  const K *src = static_cast<const K *>((level & 1) ? p.scratch : p.keys);
+  long long h = wave_find<NT, NW>(items, m, s0, sh);
+  unsigned long long first_cnt = 0, last_cnt = 0;
+  bool first_seg = true;
+  for (long long s = s0; s < s1 && h < m; ++h) {
+    const long long begin = __ldcg(&items[h].begin), end = __ldcg(&items[h].end);
+    const long long koff = __ldcg(&items[h].koff);
+    const long long a = s - koff, b = min(s1 - koff, end - begin - 1);  // item offsets
+    const K key = __ldcg(src + begin);  // Step 1
+    const long long f = begin + 1, base = tile_base(src, begin);
+    unsigned cnt = 0;
+    for (long long lo = base + ((f + a - base) / TILE) * TILE; lo < f + b; lo += TILE) {
+      const int vlo = (int)max(f + a - lo, 0ll), vhi = (int)min(f + b - lo, (long long)TILE);
+      K x[IPT];
+      wave_load<K, NT, IPT>(src, lo, vlo, vhi, x);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+          const int k = (v * NT + (int)threadIdx.x) * VEC + l;
+          cnt += (k >= vlo && k < vhi && goes_left(key, x[v * VEC + l])) ? 1u : 0u;  // Step 3
+        }
+      }
+    }
+    const unsigned long long c = wave_sum<NW>(cnt, sh);
+    if (first_seg) first_cnt = c;
+    last_cnt = c;
+    first_seg = false;
+    s = koff + b;
+  }
+  if (threadIdx.x == 0) {
+    p.wave_cnt[2 * blockIdx.x] = first_cnt;
+    p.wave_cnt[2 * blockIdx.x + 1] = last_cnt;
+  }
+}
+
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) wave_scatter_kernel(SortParams p,
+                                                                               int level) {
+  constexpr int TILE = NT * IPT, VEC = Vec<K>::N, NV = IPT / VEC, NW = NT / 32;
+  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0, "bad tile shape");
+  __shared__ __align__(16) K sout[TILE + VEC];  // + room for copy_out_v's reads
+  __shared__ WaveShared<NW> sh;
+  grid_dep_wait();
+  grid_dep_launch();
+  Control *ctl = p.ctl;
+  long long m = 0, per = 0, s0 = 0, s1 = 0;
+  if (!wave_level_span(p, level, TILE, &m, &per, &s0, &s1)) return;
+  const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
+  const WaveItem *items = p.wave_items + (size_t)(level & 1) * p.wave_cap;
+  WaveItem *next = p.wave_items + (size_t)((level + 1) & 1) * p.wave_cap;
+  K *const buf0 = static_cast<K *>(p.keys);
+  const K *src = static_cast<const K *>((level & 1) ? p.scratch : p.keys);
+  K *dst = static_cast<K *>((level & 1) ? p.keys : p.scratch);
+  const unsigned cflags = (level & 1) ? 0u : kItemScratch;  // the sides live in dst
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  long long h = wave_find<NT, NW>(items, m, s0, sh);
+
+  // less keys of the first sub-array before this span: the last count of the CTA
+  // holding its first key, and the (only) count of every CTA in between
+  unsigned long long E = 0;
+  {
+    const long long koff = __ldcg(&items[h].koff);
+    if (koff < s0) {
+      const long long cf = koff / per;
+      unsigned long long part = 0;
+      for (long long j = cf + tid; j < (long long)blockIdx.x; j += NT)
+        part += __ldcg(&p.wave_cnt[2 * j + (j == cf ? 1 : 0)]);
+      E = wave_sum<NW>(part, sh);
+    }
+  }
+  unsigned long long st_items = 0, st_keys = 0, st_tiles = 0;
+  for (long long s = s0; s < s1 && h < m; ++h) {
+    const long long begin = __ldcg(&items[h].begin), end = __ldcg(&items[h].end);
+    const long long koff = __ldcg(&items[h].koff);
+    const long long klen = end - begin - 1;
+    const long long a = s - koff, b = min(s1 - koff, klen);
+    const K key = __ldcg(src + begin);  // Step 1
+    const long long f = begin + 1, base = tile_base(src, begin);
+    for (long long lo = base + ((f + a - base) / TILE) * TILE; lo < f + b; lo += TILE) {
+      const int vlo = (int)max(f + a - lo, 0ll), vhi = (int)min(f + b - lo, (long long)TILE);
+      K x[IPT];
+      wave_load<K, NT, IPT>(src, lo, vlo, vhi, x);
+      // Step 3 per key, then one warp scan of the packed (less, >=) counts
+      unsigned lessbits = 0, gebits = 0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+#pragma unroll
+        for (int l = 0; l < VEC; ++l) {
+          const int j = v * VEC + l, k = (v * NT + tid) * VEC + l;
+          const bool valid = k >= vlo && k < vhi;
+          const bool le = goes_left(key, x[j]);
+          lessbits |= (unsigned)(valid && le) << j;
+          gebits |= (unsigned)(valid && !le) << j;
+        }
+      }
+      const unsigned mine = (unsigned)__popc(lessbits) | ((unsigned)__popc(gebits) << 16);
+      unsigned incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += u;
+      }
+      if (lane == 31) {
+        sh.wl[w] = incl & 0xffffu;
+        sh.wg[w] = incl >> 16;
+      }
+      __syncthreads();
+      unsigned L = 0, G = 0, wlx = 0, wgx = 0;
+#pragma unroll
+      for (int i = 0; i < NW; ++i) {
+        const unsigned c0 = sh.wl[i], c1 = sh.wg[i];
+        if (i < w) {
+          wlx += c0;
+          wgx += c1;
+        }
+        L += c0;
+        G += c1;
+      }
+      scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
+      __syncthreads();
+      // less keys after the E less keys before this tile; >= keys before the >= keys of
+      // earlier tiles, counted from the right end
+      const long long before = lo + vlo - f;  // keys of the sub-array before this tile
+      const long long lbase = begin + (long long)E;
+      const long long gbase = end - (before - (long long)E) - (long long)G;
+      if (!(lbase >= begin && lbase + L <= end && gbase >= begin && gbase + G <= end)) {
+        if (tid == 0) raise_error(ctl, kDevInternal, 0x900000000ull | (unsigned)h);
+        break;  // uniform: every thread computed the same bounds
+      }
+      copy_out_v<K, NT>(sout, dst + lbase, L, tid);
+      copy_out_v<K, NT>(sout + L, dst + gbase, G, tid);
+      E += L;
+      ++st_tiles;
+      __syncthreads();  // sout and the warp counts are reused by the next tile
+    }
+    if (koff + klen <= s1 && tid == 0) {
+      // this span holds the sub-array's last key: E = #{x < key}
+      const long long kpos = begin + (long long)E;  // Step 4
+      if (kpos >= end) {
+        raise_error(ctl, kDevInternal, 0x800000000ull | (unsigned)h);
+      } else {
+        if (level & 1) {
+          buf0[kpos] = key;
+        } else {
+          const unsigned long long i = atomicAdd(&ctl->wave_fin, 1ull);
+          if (i < p.wave_cap) {
+            p.wave_fin[2 * i] = (unsigned long long)kpos;
+            p.wave_fin[2 * i + 1] = key_bits<K>(key);
+          } else {
+            raise_error(ctl, kDevWorkspaceExhausted, 4);
+          }
+        }
+        ++st_items;
+        st_keys += (unsigned long long)(end - begin);
+        const long long cb[2] = {begin, kpos + 1}, ce[2] = {kpos, end};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {  // Steps 5-6
+          const long long mm = ce[c] - cb[c];
+          if (mm > p.cutoff) {
+            const unsigned long long old = atomicAdd(
+                &ctl->wave_ctr[(level + 1) & 1], (1ull << kWaveKeyBits) | (unsigned long long)(mm - 1));
+            const unsigned long long idx = old >> kWaveKeyBits;
+            if (idx < p.wave_cap) {
+              next[idx].begin = cb[c];
+              next[idx].end = ce[c];
+              next[idx].koff = (long long)(old & kWaveKeyMask);
+            } else {
+              raise_error(ctl, kDevWorkspaceExhausted, 3);
+            }
+          } else if (mm >= 2 || (mm == 1 && cflags)) {
+            // small sides (and single keys left in buffer 1) go to the SMEM finisher
+            unsigned long long t0 = 0;
+            unsigned tiles = 0;
+            reserve_item<K, TILE>(p, epoch, cb[c], ce[c], cflags, &t0, &tiles);
+          }
+        }
+      }
+    }
+    E = 0;  // the next sub-array starts inside this span
+    s = koff + b;
+  }
+  if (tid == 0) {
+    if (st_items) atomicAdd(&ctl->large_items, st_items);
+    if (st_keys) atomicAdd(&ctl->large_keys, st_keys);
+    if (st_tiles) atomicAdd(&ctl->tiles, st_tiles);
+  }
+}
+
+// After the last wave level: keys still waiting go to buffer 0, and every sub-array on
+// the list becomes a work item of tile_kernel's queue (ticket map published).
+template <typename K, int TILE>
+__global__ void wave_handoff_kernel(SortParams p, int level) {
+  grid_dep_wait();
+  Control *ctl = p.ctl;
+  if (level & 1) wave_place_late_keys<K>(p);
+  const unsigned long long ctr = __ldcg(&ctl->wave_ctr[level & 1]);
+  const long long m = (long long)(ctr >> kWaveKeyBits);
+  if (m == 0 || m > (long long)p.wave_cap || __ldcg(&ctl->abort) != 0u) return;
+  const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
+  const WaveItem *items = p.wave_items + (size_t)(level & 1) * p.wave_cap;
+  const unsigned flags = (level & 1) ? kItemScratch : 0u;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long h = (long long)blockIdx.x * blockDim.x + threadIdx.x; h < m; h += stride) {
+    unsigned long long t0 = 0;
+    unsigned tiles = 0;
+    const unsigned long long idx =
+        reserve_item<K, TILE>(p, epoch, __ldcg(&items[h].begin), __ldcg(&items[h].end), flags,
+                              &t0, &tiles);
+    if (tiles) publish_tickets(p, epoch, idx, t0, tiles, 0, 1);
+  }
+}
+
 // Phase 2: every small sub-array, claimed from the complete list, is loaded into shared
 // memory and finished by smem_ksort. Dynamic shared memory: A and B (cutoff keys
 // each), then the per-warp leaf lists.
@@ -2473,6 +2833,23 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(SortParams p) {
   }
 }
 
+// Wave form: a root above the cutoff goes on the level-0 list (true), else false.
+__device__ __forceinline__ bool seed_wave_root(const SortParams &p, long long b, long long e) {
+  if (!p.wave || e - b <= p.cutoff || (p.root_flags & kItemPartitionOnly)) return false;
+  Control *ctl = p.ctl;
+  const unsigned long long old = atomicAdd(
+      &ctl->wave_ctr[0], (1ull << kWaveKeyBits) | (unsigned long long)(e - b - 1));
+  const unsigned long long idx = old >> kWaveKeyBits;
+  if (idx < p.wave_cap) {
+    p.wave_items[idx].begin = b;
+    p.wave_items[idx].end = e;
+    p.wave_items[idx].koff = (long long)(old & kWaveKeyMask);
+  } else {
+    raise_error(ctl, kDevWorkspaceExhausted, 5);
+  }
+  return true;
+}
+
 // Seed kernel (one CTA): starts a new generation and queues the roots.
 template <typename K, int TILE>
 __global__ void seed_kernel(SortParams p) {
@@ -2491,6 +2868,8 @@ __global__ void seed_kernel(SortParams p) {
     ctl->large_items = ctl->large_keys = ctl->tiles = 0;
     ctl->small_items = ctl->small_keys = 0;
     ctl->smem_levels = ctl->lookback_steps = 0;
+    ctl->wave_ctr[0] = ctl->wave_ctr[1] = 0;
+    ctl->wave_fin = 0;
     epoch_sh = ep;
   }
   __syncthreads();
@@ -2503,7 +2882,8 @@ __global__ void seed_kernel(SortParams p) {
       tiles_sh = 0;
       if (p.total >= 2) {
         if (p.total > kMaxItemKeys) raise_error(ctl, kDevBadOffsets, 0);
-        else idx_sh = reserve_item<K, TILE>(p, epoch, 0, p.total, p.root_flags, &t0_sh, &tiles_sh);
+        else if (!seed_wave_root(p, 0, p.total))
+          idx_sh = reserve_item<K, TILE>(p, epoch, 0, p.total, p.root_flags, &t0_sh, &tiles_sh);
       }
     }
     __syncthreads();
@@ -2516,7 +2896,7 @@ __global__ void seed_kernel(SortParams p) {
       raise_error(ctl, kDevBadOffsets, (unsigned long long)r);
       continue;
     }
-    if (e - b >= 2) {
+    if (e - b >= 2 && !seed_wave_root(p, b, e)) {
       unsigned long long t0 = 0;
       unsigned tiles = 0;
       const unsigned long long idx = reserve_item<K, TILE>(p, epoch, b, e, p.root_flags, &t0, &tiles);

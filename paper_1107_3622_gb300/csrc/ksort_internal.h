@@ -50,6 +50,21 @@ struct alignas(128) Control {
   // the last CTA of a call finishes)
   unsigned part_done, part_abort;
   unsigned long long pad1[2];
+  // level-synchronous passes: per level parity, items << kWaveKeyBits | classified keys
+  unsigned long long wave_ctr[2];
+  unsigned long long wave_fin;  // keys of an even level waiting for their final index
+};
+
+// Level-synchronous partition passes (the wave form): the sub-arrays above the cutoff
+// at one recursion depth form a list, and their classified keys (all but each key)
+// are numbered consecutively in list order, the level's key space.
+constexpr int kWaveKeyBits = 40;
+constexpr unsigned long long kWaveKeyMask = (1ull << kWaveKeyBits) - 1ull;
+struct alignas(16) WaveItem {
+  long long begin;  // sub-array [begin, end); its key is the element at begin
+  long long end;
+  long long koff;   // level key-space index of the element at begin + 1
+  long long pad;
 };
 
 // One work item: a sub-array [begin, end) whose first element is its key.
@@ -90,15 +105,26 @@ struct SortParams {
   long long readable[2];     // elements [0, readable[j]) of buffer j may be read in bulk
   unsigned long long *trace; // optional: kTraceWords timestamps per tile ticket
   long long trace_cap;       // tickets the trace buffer holds
+  // wave form: two level lists of wave_cap items (level parity), two less counts per
+  // CTA of a level pass, and wave_cap (index, key bits) pairs of keys placed late
+  WaveItem *wave_items;
+  unsigned long long wave_cap;
+  unsigned long long *wave_cnt;
+  unsigned long long *wave_fin;
+  int wave;                  // nonzero: the seed queues large roots on the level-0 list
 };
 constexpr int kTraceWords = 8;
 
 // Host-side launch interface, one explicit instantiation per key type. `variant`
 // selects one of kTileVariants compiled forms of the tile passes, for three CTA shapes
 // each: tile_kernel (variants 0-2, keys loaded into registers), tile_pipe_kernel (3-5,
-// staged through shared memory by bulk copies) and tile_ws_kernel (6-8, warp roles).
+// staged through shared memory by bulk copies), tile_ws_kernel (6-8, warp roles) and
+// the wave form (9-11: level-synchronous passes for the upper levels, then tile_kernel
+// of the same shape for what remains).
 constexpr int kTileShapes = 3;
-constexpr int kTileForms = 3;
+constexpr int kTileForms = 4;
+constexpr int kWaveForm = 3;
+constexpr int kWaveMaxGrid = 4096;  // CTAs of one level pass (two counts each)
 constexpr int kTileVariants = kTileForms * kTileShapes;
 
 struct KernelInfo {
@@ -106,7 +132,7 @@ struct KernelInfo {
   int tile_keys;      // keys per tile pass
   int max_cutoff;     // largest shared-memory item the kernels support
   int keys_per_thread;
-  int form;           // 0 tile_kernel, 1 tile_pipe_kernel, 2 tile_ws_kernel
+  int form;           // 0 tile_kernel, 1 tile_pipe_kernel, 2 tile_ws_kernel, 3 wave
 };
 
 template <typename K>
@@ -126,6 +152,14 @@ struct Launcher {
   static size_t exact_work_bytes(long long n);
   static cudaError_t exact(const void *in, void *out, long long n, long long *key_index,
                            void *work, cudaStream_t s);
+  // wave form, CTA shape `shape`: CTAs per SM of a level pass; one level (count and
+  // scatter launches, chained by programmatic dependent launch when `pdl`); hand-off of
+  // the list of level `level` to the work queue of tile_kernel
+  static cudaError_t wave_occupancy(int shape, int *ctas);
+  static cudaError_t wave_level(const SortParams &p, int shape, int level, int grid, bool pdl,
+                                cudaStream_t s);
+  static cudaError_t wave_handoff(const SortParams &p, int shape, int level, bool pdl,
+                                  cudaStream_t s);
 };
 
 }  // namespace ksort

@@ -24,14 +24,15 @@ template <> struct Shapes<double> {
 };
 
 // Variant V: CTA shape V % kTileShapes in form V / kTileShapes (0 registers, 1 staged,
-// 2 warp roles, whose tile is the data warps' share: two warps load and look back).
+// 2 warp roles, whose tile is the data warps' share: two warps load and look back; 3
+// wave levels, whose work queue then runs form 0 of the same shape).
 template <typename K, int V>
 struct ShapeOf {
   static constexpr int FORM = V / kTileShapes;
   static constexpr int NT = Shapes<K>::NT[V % kTileShapes];
   static constexpr int IPT = Shapes<K>::IPT[V % kTileShapes];
   static constexpr int TILE = (FORM == 2 ? NT - 64 : NT) * IPT;
-  static constexpr bool STAGED = FORM != 0;
+  static constexpr bool STAGED = FORM == 1 || FORM == 2;
   static constexpr size_t SMEM = FORM == 2   ? dev::ws_smem_bytes<K, TILE>()
                                  : STAGED    ? dev::pipe_smem_bytes<K, TILE>()
                                              : 0;
@@ -49,6 +50,9 @@ decltype(auto) with_shape(int v, F &&f) {
     case 6: return f(ShapeOf<K, 6>{});
     case 7: return f(ShapeOf<K, 7>{});
     case 8: return f(ShapeOf<K, 8>{});
+    case 9: return f(ShapeOf<K, 9>{});
+    case 10: return f(ShapeOf<K, 10>{});
+    case 11: return f(ShapeOf<K, 11>{});
     default: return f(ShapeOf<K, 0>{});
   }
 }
@@ -170,6 +174,61 @@ cudaError_t Launcher<K>::partition(const SortParams &p, int shape, int grid, cud
     if (e != cudaSuccess) return e;
     fn<<<grid, S::NT, smem, st>>>(p);
     return cudaGetLastError();
+  });
+}
+
+// ------------------------------------------------------------------ wave form
+// One launch of fn(p, level), under programmatic dependent launch when `pdl` (the
+// kernel then starts as the previous launch's CTAs leave and waits for its memory).
+inline cudaError_t launch_level(void (*fn)(SortParams, int), int grid, int block,
+                                const SortParams &p, int level, bool pdl, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, fn, p, level);
+}
+
+template <typename K>
+cudaError_t Launcher<K>::wave_occupancy(int shape, int *ctas) {
+  return with_shape<K>(shape % kTileShapes, [&](auto s) {
+    using S = decltype(s);
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, dev::wave_scatter_kernel<K, S::NT, S::IPT>, S::NT, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &b, dev::wave_count_kernel<K, S::NT, S::IPT>, S::NT, 0);
+    *ctas = a < b ? a : b;
+    return e;
+  });
+}
+
+template <typename K>
+cudaError_t Launcher<K>::wave_level(const SortParams &p, int shape, int level, int grid, bool pdl,
+                                    cudaStream_t st) {
+  return with_shape<K>(shape % kTileShapes, [&](auto s) {
+    using S = decltype(s);
+    cudaError_t e = launch_level(dev::wave_count_kernel<K, S::NT, S::IPT>, grid, S::NT, p,
+                                 level, pdl, st);
+    if (e != cudaSuccess) return e;
+    return launch_level(dev::wave_scatter_kernel<K, S::NT, S::IPT>, grid, S::NT, p, level, pdl,
+                        st);
+  });
+}
+
+template <typename K>
+cudaError_t Launcher<K>::wave_handoff(const SortParams &p, int shape, int level, bool pdl,
+                                      cudaStream_t st) {
+  return with_shape<K>(shape % kTileShapes, [&](auto s) {
+    using S = decltype(s);
+    return launch_level(dev::wave_handoff_kernel<K, S::NT * S::IPT>, 64, 256, p, level, pdl, st);
   });
 }
 

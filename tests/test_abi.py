@@ -93,28 +93,35 @@ def test_oracle_and_library_share_no_code():
 def test_tile_shapes_and_tuning_fields(lib):
     import paper_1107_3622_gb300 as ks
     for code in (ks.F32, ks.F64, ks.U32):
-        shapes = [ks.ksort_tile_shape(code, s) for s in range(1, 10)]
+        shapes = [ks.ksort_tile_shape(code, s) for s in range(1, 13)]
         vec = 2 if code == ks.F64 else 4
         for nt, ipt, _ in shapes:
             assert nt % 32 == 0 and ipt % vec == 0 and ipt <= 32
-        assert len(set(shapes)) == 9
-        assert [fm for _, _, fm in shapes] == [0] * 3 + [1] * 3 + [2] * 3
+        assert len(set(shapes)) == 12
+        assert [fm for _, _, fm in shapes] == [0] * 3 + [1] * 3 + [2] * 3 + [3] * 3
         assert [s[:2] for s in shapes[:3]] == [s[:2] for s in shapes[3:6]] == \
-            [s[:2] for s in shapes[6:]]
+            [s[:2] for s in shapes[6:9]] == [s[:2] for s in shapes[9:]]
         with pytest.raises(ks.KSortError):
             ks.ksort_tile_shape(code, 0)
         with pytest.raises(ks.KSortError):
-            ks.ksort_tile_shape(code, 10)
+            ks.ksort_tile_shape(code, 13)
         before = ks.ksort_get_tuning(code)
-        assert before["tile_shape"] in range(1, 10)
+        assert before["tile_shape"] in range(1, 13)
+        assert before["wave_levels"] == -1 or before["wave_levels"] in range(1, 65)
         with pytest.raises(ks.KSortError):
-            ks.ksort_set_tuning(code, tile_shape=10)
+            ks.ksort_set_tuning(code, tile_shape=13)
         with pytest.raises(ks.KSortError):
             ks.ksort_set_tuning(code, ctas_per_sm=-2)
+        for bad in (-2, 65):
+            with pytest.raises(ks.KSortError):
+                ks.ksort_set_tuning(code, wave_levels=bad)
         ks.ksort_set_tuning(code, tile_shape=2)
         nt, ipt, _ = shapes[1]
         assert ks.ksort_tile_keys(code) == nt * ipt
-        ks.ksort_set_tuning(code, tile_shape=before["tile_shape"])
+        ks.ksort_set_tuning(code, tile_shape=11, wave_levels=7)
+        assert ks.ksort_tile_keys(code) == nt * ipt  # the wave form keeps the CTA shape's tile
+        assert ks.ksort_get_tuning(code)["wave_levels"] == 7
+        ks.ksort_set_tuning(code, tile_shape=before["tile_shape"], wave_levels=-1)
         assert ks.ksort_get_tuning(code) == before
     # shared-memory staging of two cutoff-sized buffers must fit a CTA (227 KB)
     assert 2 * 8 * ks.ksort_max_cutoff(ks.F64) <= 227 * 1024

@@ -44,7 +44,7 @@ def _oracle(ref, a):
     return b
 
 
-@pytest.mark.parametrize("shape", list(range(1, 10)))
+@pytest.mark.parametrize("shape", list(range(1, 13)))
 @pytest.mark.parametrize("dtype", list(DTYPES))
 def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
     import torch
@@ -66,7 +66,7 @@ def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
         assert np.sort(got[i + 1:]).tobytes() == np.sort(b[ri + 1:]).tobytes()
 
 
-@pytest.mark.parametrize("shape", list(range(1, 10)))
+@pytest.mark.parametrize("shape", list(range(1, 13)))
 def test_tile_shapes_batched(ref, ks, restore, shape):
     import torch
     ks.ksort_set_tuning(0, tile_shape=shape)

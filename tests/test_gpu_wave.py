@@ -1,0 +1,163 @@
+"""The wave form of the sort (tile shapes 10-12): the upper recursion levels run level by
+level, each as a counting launch and a moving launch over equal key spans per CTA, then
+the work queue finishes what remains. Every result must stay byte-identical to the
+oracle whatever the number of wave levels (the hand-off to the queue can happen at any
+depth), at both ends of the cutoff range, on degenerate and duplicate-heavy inputs, on
+batches (many roots on one level list) and under CUDA-graph capture."""
+import numpy as np
+import pytest
+
+import ksort_inputs as gen
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = {"f32": 0, "f64": 1, "u32": 2}
+WAVE = (10, 11, 12)
+
+
+@pytest.fixture(scope="module")
+def ks():
+    import torch
+    import paper_1107_3622_gb300 as ks
+    ks.load()
+    torch.cuda.set_device(0)
+    return ks
+
+
+@pytest.fixture
+def restore(ks):
+    saved = {c: ks.ksort_get_tuning(c) for c in DTYPES.values()}
+    yield
+    for c, t in saved.items():
+        ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
+                            tile_shape=t["tile_shape"], wave_levels=t["wave_levels"])
+
+
+def _dev(a):
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def _sort(ks, code, a):
+    t = _dev(a)
+    ks.ksort_sort(code, t, len(a))
+    assert ks.ksort_get_device_error() == 0
+    return t.cpu().numpy().view(a.dtype)
+
+
+def _oracle(ref, a):
+    b = a.copy()
+    ref.sort(b)
+    return b
+
+
+@pytest.mark.parametrize("shape", WAVE)
+@pytest.mark.parametrize("dtype", list(DTYPES))
+def test_wave_sort_sizes(ref, ks, restore, dtype, shape):
+    code = DTYPES[dtype]
+    ks.ksort_set_tuning(code, tile_shape=shape, wave_levels=-1)
+    assert ks.ksort_tile_shape(code, shape)[2] == 3
+    tile = ks.ksort_tile_keys(code)
+    for n in (2, 3, 100, tile - 1, tile + 1, 3 * tile + 5, 250_003, 1_000_000):
+        a = gen.make("uniform", dtype, n, gen.seed_for(9, shape, n % 1009))
+        assert _sort(ks, code, a).tobytes() == _oracle(ref, a).tobytes(), n
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3, 5, 8, 24])
+def test_wave_levels_any_handoff_depth(ref, ks, restore, levels):
+    """The hand-off from the level lists to the work queue at any depth, including
+    after the lists have emptied (24 levels), gives the same bytes."""
+    for dtype, code in DTYPES.items():
+        ks.ksort_set_tuning(code, tile_shape=10, wave_levels=levels, cutoff=1024)
+        a = gen.make("uniform", dtype, 700_001, gen.seed_for(9, 20 + levels, code))
+        assert _sort(ks, code, a).tobytes() == _oracle(ref, a).tobytes(), dtype
+
+
+@pytest.mark.parametrize("cutoff", [2, 33, 1024, 16384])
+def test_wave_cutoff_extremes(ref, ks, restore, cutoff):
+    for dtype, code in DTYPES.items():
+        c = min(cutoff, ks.ksort_max_cutoff(code))
+        ks.ksort_set_tuning(code, tile_shape=11, cutoff=c, wave_levels=-1)
+        for pattern in ("uniform", "distinct16"):
+            a = gen.make(pattern, dtype, 60_000, gen.seed_for(9, 30, c))
+            assert _sort(ks, code, a).tobytes() == _oracle(ref, a).tobytes(), (dtype, pattern)
+
+
+@pytest.mark.parametrize("pattern", ["sorted", "reverse", "distinct16", "organ_pipe",
+                                     "quantized15"])
+def test_wave_stress_patterns(ref, ks, restore, pattern):
+    """Degenerate orders keep one large sub-array per level (every level a single
+    shrinking item); duplicate runs peel one key per partition."""
+    for dtype, code in DTYPES.items():
+        ks.ksort_set_tuning(code, tile_shape=10, wave_levels=6)
+        n = 50_000 if pattern in ("sorted", "reverse", "organ_pipe") else 400_000
+        a = gen.make(pattern, dtype, n, gen.seed_for(9, 40, n))
+        assert _sort(ks, code, a).tobytes() == _oracle(ref, a).tobytes(), (dtype, pattern)
+
+
+@pytest.mark.parametrize("dtype", list(DTYPES))
+def test_wave_table1_size(ref, ks, restore, dtype):
+    code = DTYPES[dtype]
+    ks.ksort_set_tuning(code, tile_shape=10, wave_levels=-1)
+    n = {"f32": 7_000_000, "f64": 10_000_000, "u32": 2_500_000}[dtype]
+    a = gen.make("uniform", dtype, n, gen.seed_for(9, 50, 0))
+    assert _sort(ks, code, a).tobytes() == _oracle(ref, a).tobytes()
+
+
+def test_wave_batched_and_graph(ref, ks, restore):
+    import torch
+    ks.ksort_set_tuning(ks.F32, tile_shape=10, wave_levels=-1)
+    lengths = gen.batched_lengths(300, 2, 200_000, seed=gen.seed_for(9, 60, 0))
+    lengths[5] = 0
+    lengths[7] = 1
+    lengths[11] = 1_000_000
+    off = gen.offsets_from_lengths(lengths)
+    flat = gen.uniform_f32(gen.seed_for(9, 61, 0), int(off[-1]))
+    want = flat.copy()
+    ref.sort_batched(want, off)
+    pristine = _dev(flat)
+    offs = _dev(off)
+    keys = pristine.clone()
+    ks.sort_batched_(keys, offs)
+    assert ks.ksort_get_device_error() == 0
+    assert keys.cpu().numpy().tobytes() == want.tobytes()
+    # the same call captured once and replayed
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ks.ksort_reserve_workspace(ks.F32, int(off[-1]), len(lengths), stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    keys = pristine.clone()
+    with torch.cuda.graph(g, stream=s):
+        ks.sort_batched_(keys, offs, stream=s)
+    for _ in range(3):
+        keys.copy_(pristine)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert keys.cpu().numpy().tobytes() == want.tobytes()
+    assert ks.ksort_get_device_error(s) == 0
+
+
+def test_wave_stats_and_bad_offsets(ks, restore):
+    ks.ksort_set_tuning(ks.F32, tile_shape=10, wave_levels=-1)
+    n = 1_000_000
+    t = _dev(gen.uniform_f32(gen.seed_for(9, 70, 0), n))
+    ks.sort_(t)
+    st = ks.ksort_get_stats()
+    assert st["large_keys"] >= n and st["small_keys"] <= n
+    assert st["tiles"] >= st["large_items"] >= 1
+    # queue entries: the small items plus large items handed to the queue
+    assert st["small_items"] <= st["items_pushed"] <= st["large_items"] + st["small_items"]
+    flat = _dev(gen.uniform_f32(1, 10_000))
+    bad = _dev(np.array([0, 6000, 4000, 10_000], np.int64))
+    ks.sort_batched_(flat, bad)
+    assert ks.ksort_get_device_error() == 6
+    good = _dev(np.array([0, 5000, 10_000], np.int64))
+    ks.sort_batched_(flat, good)
+    assert ks.ksort_get_device_error() == 0
+    h = flat.cpu().numpy()
+    assert np.all(np.diff(h[:5000]) >= 0) and np.all(np.diff(h[5000:]) >= 0)
