@@ -2782,6 +2782,299 @@ __global__ void wave_handoff_kernel(SortParams p, int level) {
   }
 }
 
+// ----------------------------------------------------------------------------- partition rounds
+// Steps 1-4 on one array as one cooperative launch (one CTA per SM, all co-resident),
+// for the wave form. The classified keys (positions 1 .. n-1) are cut into rounds of
+// gridDim.x chunks of C keys; in round r, CTA c owns chunk r * gridDim.x + c, and each
+// warp a contiguous slice of it. Per round:
+//   stage    the chunk is copied into shared memory by bulk copies completing on an
+//            mbarrier (the next round's chunk is in flight while the current one is
+//            scattered);
+//   count    each warp counts its less keys (Step 3) with one ballot per 32 keys, and
+//            the CTA publishes its total;
+//   barrier  one bounded grid barrier;
+//   scatter  the CTA's less prefix is the less keys of earlier rounds plus the counts
+//            of the CTAs before it in this round; each warp then compacts its slice
+//            with ballots straight to global memory: less keys from the left end,
+//            >= keys from the right end, each store instruction a contiguous run.
+// After the last round CTA 0 writes the key at index #{x < key} (Step 4). Each key is
+// read once and written once, and no CTA waits on another except at the barriers.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <int NW>
+struct RoundShared {
+  unsigned wl[NW], wg[NW];
+  unsigned long long red[NW], red2[NW];
+  int ok;
+};
+
+// Grid-wide barrier of a cooperative launch. Thread 0 of every CTA arrives on a
+// counter with a release; the last one resets it and releases the next generation,
+// which thread 0 of every CTA acquires. It orders what thread 0 wrote before the
+// barrier (the data the CTAs exchange goes through thread 0). Every wait is bounded
+// (past the limit the error is set and the call's stop flag raised) and ends early when
+// the stop flag is up. Returns false when the CTA must stop.
+template <int NW>
+__device__ __forceinline__ bool round_grid_sync(Control *ctl, unsigned *stop, unsigned *gen,
+                                                unsigned long long limit_ns, RoundShared<NW> &sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned target = *gen + 1u;
+    int ok = 1;
+    // release: this thread's earlier writes (the CTA's published count) become visible
+    // to every CTA that acquires the next generation
+    const unsigned arrived = atom_add_release(&ctl->bar_count, 1u);
+    if (arrived == gridDim.x - 1u) {
+      atomicExch(&ctl->bar_count, 0u);
+      st_release_u32(&ctl->bar_gen, target);
+    } else {
+      unsigned ns = 32, polls = 0;
+      unsigned long long t0 = 0;
+      while (ld_acquire_u32(&ctl->bar_gen) != target) {
+        if ((++polls & 15u) == 0u) {
+          if (ld_relaxed(stop) != 0u) { ok = 0; break; }
+          const unsigned long long now = globaltimer();
+          if (t0 == 0) t0 = now;
+          else if (now - t0 > limit_ns) {
+            raise_error(ctl, kDevTimeout, 0xA00000000ull | blockIdx.x);
+            atomicExch(stop, 1u);
+            ok = 0;
+            break;
+          }
+        }
+        __nanosleep(ns);
+        ns = ns < 128 ? ns * 2 : 128;
+      }
+    }
+    *gen = target;
+    sh.ok = ok && ld_relaxed(stop) == 0u;
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
+// Chunk of round r for CTA c: key indices [*j0, *j1) (array positions + 1), and its
+// place in a staging buffer: index *so, chosen so that the first 16-byte chunk of the
+// global copy lands 16-byte aligned; *head keys precede that chunk.
+template <typename K>
+__device__ __forceinline__ void round_chunk(const K *in, long long m, int r, int c, int G, int C,
+                                            long long *j0, long long *j1, int *head, int *so) {
+  constexpr int V16 = 16 / (int)sizeof(K);
+  const long long a = ((long long)r * G + c) * C;
+  *j0 = a < m ? a : m;
+  *j1 = a + C < m ? a + C : m;
+  const K *gp = in + 1 + *j0;
+  const int h = (int)(((16u - (unsigned)(reinterpret_cast<uintptr_t>(gp) & 15u)) & 15u) / sizeof(K));
+  *head = h;
+  *so = (V16 - h % V16) % V16;
+}
+
+// Thread 0: the 16-byte-aligned body of chunk [j0, j1) goes to its staging buffer by
+// bulk copies (pieces of at most 64 KB) completing on `bar`; the head and tail keys
+// around it are read with plain loads by round_edges when the chunk is used.
+template <typename K>
+__device__ __forceinline__ void round_stage_bulk(const K *in, long long j0, long long j1,
+                                                 int head, int so, K *buf,
+                                                 unsigned long long *bar) {
+  constexpr int V16 = 16 / (int)sizeof(K);
+  const int n = (int)(j1 - j0);
+  const int h = head < n ? head : n;
+  const unsigned bytes = (unsigned)((n - h) / V16) * 16u;
+  const char *gp = reinterpret_cast<const char *>(in + 1 + j0 + h);
+  char *sp = reinterpret_cast<char *>(buf + so + h);
+  fence_proxy_async();  // the buffer's earlier reads come before the copy's writes
+  mbar_expect_tx(bar, bytes);
+  for (unsigned off = 0; off < bytes; off += 65536u) {
+    const unsigned len = bytes - off < 65536u ? bytes - off : 65536u;
+    bulk_g2s(sp + off, gp + off, len, bar);
+  }
+}
+
+// Whole CTA: the keys of chunk [j0, j1) outside its bulk-copied body.
+template <typename K, int NT>
+__device__ __forceinline__ void round_edges(const K *in, long long j0, long long j1, int head,
+                                            int so, K *buf) {
+  constexpr int V16 = 16 / (int)sizeof(K);
+  const int n = (int)(j1 - j0);
+  const int h = head < n ? head : n;
+  const int body_end = h + (n - h) / V16 * V16;
+  const K *gp = in + 1 + j0;
+  K *sp = buf + so;
+  for (int i = threadIdx.x; i < h; i += NT) sp[i] = __ldcg(gp + i);
+  for (int i = body_end + threadIdx.x; i < n; i += NT) sp[i] = __ldcg(gp + i);
+}
+
+template <typename K, int NT>
+__global__ void __launch_bounds__(NT, 1) part_round_kernel(SortParams p, int C) {
+  constexpr int NW = NT / 32, V16 = 16 / (int)sizeof(K);
+  extern __shared__ __align__(16) unsigned char round_smem[];
+  const int CS = C + V16;  // one staging buffer, a multiple of V16 keys
+  K *const stage0 = reinterpret_cast<K *>(round_smem);
+  __shared__ RoundShared<NW> sh;
+  __shared__ unsigned wcnt[NW];  // less keys of each warp's slice in this round
+  __shared__ __align__(8) unsigned long long bar[2];  // bulk copies into buffer 0 / 1
+  Control *ctl = p.ctl;
+  const K *in = static_cast<const K *>(p.keys);
+  K *out = static_cast<K *>(p.scratch);
+  const long long n = p.total, m = n - 1;
+  const int G = (int)gridDim.x, c = (int)blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5;
+  const unsigned lt = lanemask_lt();
+  const K key = __ldcg(in);  // Step 1: the first element is the key
+  const int R = (int)((m + (long long)G * C - 1) / ((long long)G * C));
+  unsigned gen = 0;
+  if (tid == 0) gen = ld_acquire_u32(&ctl->bar_gen);  // the same in every CTA until all arrive
+  long long j0 = 0, j1 = 0;
+  int head = 0, so = 0;
+  round_chunk<K>(in, m, 0, c, G, C, &j0, &j1, &head, &so);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    round_stage_bulk<K>(in, j0, j1, head, so, stage0, &bar[0]);
+  }
+  __syncthreads();  // no thread touches the barriers before they are initialised
+  unsigned long long running = 0;  // less keys of the earlier rounds
+  int staged = 1, consumed = 0;      // rounds whose chunk was requested / has landed
+  bool ok = true;
+  for (int r = 0; r < R && ok; ++r) {
+    K *buf = stage0 + (r & 1) * CS;
+    if (r + 1 < R) {  // the next chunk streams in during this whole round
+      if (tid == 0) {
+        long long k0 = 0, k1 = 0;
+        int h2 = 0, so2 = 0;
+        round_chunk<K>(in, m, r + 1, c, G, C, &k0, &k1, &h2, &so2);
+        round_stage_bulk<K>(in, k0, k1, h2, so2, stage0 + ((r + 1) & 1) * CS, &bar[(r + 1) & 1]);
+      }
+      staged = r + 2;
+    }
+    round_chunk<K>(in, m, r, c, G, C, &j0, &j1, &head, &so);
+    const int nloc = (int)(j1 - j0);
+    // warp w owns the slice [w0, w1) of the chunk, whole 32-key groups but the last
+    const int S = (nloc + NW * 32 - 1) / (NW * 32) * 32;
+    const int w0 = min(w * S, nloc), w1 = min(w0 + S, nloc);
+    round_edges<K, NT>(in, j0, j1, head, so, buf);
+    if (!mbar_wait(&bar[r & 1], (unsigned)(r >> 1) & 1u, p.spin_limit_ns)) {
+      if (tid == 0) {
+        raise_error(ctl, kDevTimeout, 0xC00000000ull | (unsigned)c);
+        atomicExch(&ctl->part_abort, 1u);
+      }
+      ok = false;
+    }
+    if (__syncthreads_or(!ok)) ok = false;
+    if (!ok) break;
+    consumed = r + 1;
+    const K *sp = buf + so;
+    unsigned cnt = 0;
+    for (int g = w0; g < w1; g += 128) {  // Step 3, one ballot per 32 keys, 4 in flight
+      bool le[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = g + u * 32 + lane;
+        le[u] = i < w1 && goes_left(key, sp[i < w1 ? i : w0]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) cnt += __popc(__ballot_sync(kFull, le[u]));
+    }
+    if (lane == 0) wcnt[w] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long t = 0;
+#pragma unroll
+      for (int i = 0; i < NW; ++i) t += wcnt[i];
+      p.wave_cnt[(size_t)(r & 1) * G + c] = t;
+    }
+    if (!(ok = round_grid_sync<NW>(ctl, &ctl->part_abort, &gen, p.spin_limit_ns, sh))) break;
+    // less keys before this chunk: earlier rounds, then the CTAs before it in this round
+    unsigned long long before_c = 0, total = 0;
+    for (int q = tid; q < G; q += NT) {
+      const unsigned long long v = __ldcg(&p.wave_cnt[(size_t)(r & 1) * G + q]);
+      total += v;
+      if (q < c) before_c += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      before_c += __shfl_xor_sync(kFull, before_c, o);
+      total += __shfl_xor_sync(kFull, total, o);
+    }
+    if (lane == 0) {
+      sh.red[w] = before_c;
+      sh.red2[w] = total;
+    }
+    __syncthreads();
+    before_c = total = 0;
+    unsigned before_w = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+      before_c += sh.red[i];
+      total += sh.red2[i];
+      if (i < w) before_w += wcnt[i];
+    }
+    // this warp's less keys go to out[lb ...]; its >= keys fill [gb, gb + its >= count)
+    // from the left, after the >= keys of every later slice: counted from the right end
+    long long lb = (long long)(running + before_c) + before_w;
+    const long long ge_before = (j0 + w0) - lb;  // >= keys before this slice
+    long long gb = n - ge_before - (long long)((w1 - w0) - (int)wcnt[w]);
+    if (!(lb >= 0 && lb + wcnt[w] <= n && gb >= 0 && gb + ((w1 - w0) - (int)wcnt[w]) <= n)) {
+      if (lane == 0) {
+        raise_error(ctl, kDevInternal, 0xB00000000ull | (unsigned)c);
+        atomicExch(&ctl->part_abort, 1u);
+      }
+      ok = false;
+    }
+    if (__syncthreads_or(!ok)) ok = false;
+    if (!ok) break;
+    for (int g = w0; g < w1; g += 128) {  // four groups of 32 keys in flight
+      K x[4];
+      unsigned bl[4], bg[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = g + u * 32 + lane;
+        const bool valid = i < w1;
+        x[u] = sp[valid ? i : w0];
+        const bool le = valid && goes_left(key, x[u]);
+        bl[u] = __ballot_sync(kFull, le);
+        bg[u] = __ballot_sync(kFull, valid && !le);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if ((bl[u] >> lane) & 1u) out[lb + __popc(bl[u] & lt)] = x[u];
+        else if ((bg[u] >> lane) & 1u) out[gb + __popc(bg[u] & lt)] = x[u];
+        lb += __popc(bl[u]);
+        gb += __popc(bg[u]);
+      }
+    }
+    running += total;
+    __syncthreads();  // wcnt and the buffer are reused two rounds on
+  }
+  if (tid == 0) {
+    // a chunk requested but not used (a stopped call) may still be landing: wait for it,
+    // bounded, before the CTA's shared memory is released
+    for (int q = consumed; q < staged; ++q)
+      (void)mbar_wait(&bar[q & 1], (unsigned)(q >> 1) & 1u, p.spin_limit_ns);
+  }
+  if (ok && c == 0 && tid == 0) {
+    out[running] = key;  // Step 4: the key's final index is #{x < key}
+    if (p.key_index) *p.key_index = (long long)running;
+  }
+  // the last CTA out leaves the barrier and stop flag clear for the next call
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl->part_done, 1u) == (unsigned)G - 1u) {
+      ctl->bar_count = 0u;
+      ctl->part_abort = 0u;
+      __threadfence();
+      ctl->part_done = 0u;
+    }
+  }
+}
+
 // Phase 2: every small sub-array, claimed from the complete list, is loaded into shared
 // memory and finished by smem_ksort. Dynamic shared memory: A and B (cutoff keys
 // each), then the per-warp leaf lists.

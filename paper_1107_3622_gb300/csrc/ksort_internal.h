@@ -53,6 +53,8 @@ struct alignas(128) Control {
   // level-synchronous passes: per level parity, items << kWaveKeyBits | classified keys
   unsigned long long wave_ctr[2];
   unsigned long long wave_fin;  // keys of an even level waiting for their final index
+  unsigned bar_count;           // grid barrier of part_round_kernel: CTAs arrived
+  unsigned bar_gen;             // and its generation (only ever incremented)
 };
 
 // Level-synchronous partition passes (the wave form): the sub-arrays above the cutoff
@@ -160,6 +162,9 @@ struct Launcher {
                                 cudaStream_t s);
   static cudaError_t wave_handoff(const SortParams &p, int shape, int level, bool pdl,
                                   cudaStream_t s);
+  // single partitions of the wave form: part_round_kernel, one cooperative launch of one
+  // CTA per SM over rounds of staged chunks (n >= 2)
+  static cudaError_t partition_rounds(const SortParams &p, int shape, int sms, cudaStream_t s);
 };
 
 }  // namespace ksort

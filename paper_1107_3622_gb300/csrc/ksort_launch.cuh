@@ -2,6 +2,8 @@
 // ksort_f32.cu / ksort_f64.cu / ksort_u32.cu, which each instantiate Launcher<K>.
 #pragma once
 
+#include <algorithm>
+
 #include "ksort_device.cuh"
 
 namespace ksort {
@@ -229,6 +231,54 @@ cudaError_t Launcher<K>::wave_handoff(const SortParams &p, int shape, int level,
   return with_shape<K>(shape % kTileShapes, [&](auto s) {
     using S = decltype(s);
     return launch_level(dev::wave_handoff_kernel<K, S::NT * S::IPT>, 64, 256, p, level, pdl, st);
+  });
+}
+
+// part_round_kernel with the CTA size of shape `shape`: one CTA per SM with two staging
+// buffers of as many keys as the device's shared memory allows (fewer when the array
+// needs fewer), launched cooperatively so that all CTAs are co-resident.
+template <typename K>
+cudaError_t Launcher<K>::partition_rounds(const SortParams &p, int shape, int sms,
+                                          cudaStream_t st) {
+  return with_shape<K>(shape % kTileShapes, [&](auto s) {
+    using S = decltype(s);
+    constexpr int V16 = 16 / (int)sizeof(K);
+    auto fn = dev::part_round_kernel<K, S::NT>;
+    int dev_id = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev_id);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    const long long room = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
+    const long long cap = room / 2 / (long long)sizeof(K) / V16 * V16 - V16;  // keys per buffer
+    if (cap < V16) return cudaErrorInvalidConfiguration;
+    const size_t smem_max = (size_t)(2 * (cap + V16)) * sizeof(K);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, S::NT, smem_max);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int g = (int)std::min<long long>((long long)sms * per_sm, kWaveMaxGrid);
+    // equal chunks for small arrays (one round), else full buffers
+    const long long m = p.total - 1;
+    const long long share = ((m + g - 1) / g + V16 - 1) / V16 * V16;
+    const long long C = std::max<long long>(V16, std::min(cap, share));
+    const size_t smem = (size_t)(2 * (C + V16)) * sizeof(K);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3((unsigned)S::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, p, (int)C);
   });
 }
 

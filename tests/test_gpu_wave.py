@@ -1,9 +1,12 @@
-"""The wave form of the sort (tile shapes 10-12): the upper recursion levels run level by
+"""The wave form (tile shapes 10-12). Sorts: the upper recursion levels run level by
 level, each as a counting launch and a moving launch over equal key spans per CTA, then
 the work queue finishes what remains. Every result must stay byte-identical to the
 oracle whatever the number of wave levels (the hand-off to the queue can happen at any
 depth), at both ends of the cutoff range, on degenerate and duplicate-heavy inputs, on
-batches (many roots on one level list) and under CUDA-graph capture."""
+batches (many roots on one level list) and under CUDA-graph capture. Single partitions:
+one cooperative launch streaming staged chunks in rounds, checked against the oracle's
+key index and side multisets for every key type, one to several rounds, unaligned
+starts, in place, and interleaved with part_kernel calls."""
 import numpy as np
 import pytest
 
@@ -161,3 +164,72 @@ def test_wave_stats_and_bad_offsets(ks, restore):
     assert ks.ksort_get_device_error() == 0
     h = flat.cpu().numpy()
     assert np.all(np.diff(h[:5000]) >= 0) and np.all(np.diff(h[5000:]) >= 0)
+
+
+def _bits(v):
+    """Multiset of bit patterns (uint32 or uint64 view), sorted, as bytes."""
+    return np.sort(v.view(np.uint64 if v.dtype.itemsize == 8 else np.uint32)).tobytes()
+
+
+def _check_partition(ref, ks, code, a, offset=0, in_place=False):
+    """One wave-form partition of `a` (placed `offset` keys into a larger device buffer,
+    so the start is not 16-byte aligned for offset % 4 != 0) against the oracle: the key
+    index, the key, and both side multisets bit for bit."""
+    import torch
+    n = len(a)
+    big = np.zeros(n + offset + 3, a.dtype)
+    big[offset:offset + n] = a
+    t = _dev(big)
+    src = t[offset:offset + n]
+    idx = torch.empty(1, dtype=torch.int64, device="cuda")
+    if in_place:
+        ks.ksort_partition(code, src, n, idx)
+        got = src.cpu().numpy().view(a.dtype)
+    else:
+        dst = torch.empty_like(src)
+        ks.ksort_partition_out(code, src, dst, n, idx)
+        got = dst.cpu().numpy().view(a.dtype)
+        assert src.cpu().numpy().view(a.dtype).tobytes() == a.tobytes()  # input untouched
+    assert ks.ksort_get_device_error() == 0
+    i = int(idx.item())
+    b = a.copy()
+    ri, *_ = ref.partition(b)
+    assert i == ri
+    assert got[i:i + 1].tobytes() == a[:1].tobytes()
+    assert _bits(got[:i]) == _bits(b[:ri]) and _bits(got[i + 1:]) == _bits(b[ri + 1:])
+
+
+@pytest.mark.parametrize("shape", WAVE)
+@pytest.mark.parametrize("dtype", list(DTYPES))
+def test_wave_partition_rounds(ref, ks, restore, dtype, shape):
+    """Single partitions of the wave form (one cooperative launch streaming staged
+    chunks in rounds): one chunk per CTA, partial rounds, and several full rounds."""
+    code = DTYPES[dtype]
+    ks.ksort_set_tuning(code, tile_shape=shape)
+    for n in (2, 3, 31, 4097, 100_003, 1_000_001, 7_000_000):
+        a = gen.make("uniform", dtype, n, gen.seed_for(9, 80 + shape, n % 1013))
+        _check_partition(ref, ks, code, a)
+    a = gen.make("uniform", dtype, 250_001, gen.seed_for(9, 90, shape))
+    for offset in (1, 2, 3):
+        _check_partition(ref, ks, code, a, offset=offset)
+    _check_partition(ref, ks, code, a, in_place=True)
+
+
+def test_wave_partition_alternates_with_part_kernel(ref, ks, restore):
+    """Calls of the cooperative partition and of part_kernel interleave on one stream
+    (both leave the shared barrier and stop flags clear), including key classes the
+    IEEE compare treats specially."""
+    for rep in range(6):
+        for shape in (10, 1, 12, 3):
+            ks.ksort_set_tuning(ks.F32, tile_shape=shape)
+            a = gen.make("distinct16" if rep % 2 else "uniform", "f32", 300_007,
+                         gen.seed_for(9, 100 + rep, shape))
+            _check_partition(ref, ks, ks.F32, a)
+    ks.ksort_set_tuning(ks.F64, tile_shape=11)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(200_003) * 10.0 ** rng.integers(-300, 300, 200_003)
+    pick = rng.random(len(a)) < 0.2
+    a[pick] = rng.choice(np.array([np.nan, -0.0, 0.0, np.inf, -np.inf, 5e-324]), int(pick.sum()))
+    for key in (np.nan, -0.0, np.inf, 1.0):
+        a[0] = key
+        _check_partition(ref, ks, ks.F64, a)
