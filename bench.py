@@ -406,7 +406,9 @@ def run_ours(args, dist: Dist):
                    "tuning": tuning},
         "roofline": roofline,
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,  # seed_kernel + tile_kernel + small_kernel per sort
+        # kernels of ours per ksort_sort, as the library counted them (seed, tile passes or
+        # wave levels, finisher), times the timed steps
+        "gpu_launches": int(stats.get("launches", 3)) * args.steps,
         "clocks": clocks.summary(),
         "timed_wall_s": round(wall, 3),
         "step_ms": {"min": round(min(step_ms), 4), "median": round(statistics.median(step_ms), 4),

@@ -164,6 +164,7 @@ typedef struct {
     uint64_t smem_levels;   /* partition levels run inside shared memory (all items)   */
     uint64_t lookback_steps;/* 32-wide look-back windows examined                      */
     uint64_t items_pushed;  /* work-queue entries used                                 */
+    uint64_t launches;      /* kernels the last sort or partition on `stream` enqueued */
 } ksort_stats_t;
 KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out);
 

@@ -51,7 +51,7 @@ class KSortError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "large_items", "large_keys", "tiles", "small_items", "small_keys",
-        "smem_levels", "lookback_steps", "items_pushed")]
+        "smem_levels", "lookback_steps", "items_pushed", "launches")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

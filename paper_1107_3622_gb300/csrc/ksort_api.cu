@@ -99,6 +99,7 @@ struct Workspace {
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
   unsigned pending_error = 0;  // device error carried over from a replaced allocation
+  unsigned long long launches = 0;  // kernels the last sort or partition on it enqueued
 };
 
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
@@ -186,7 +187,9 @@ ksort_status_t get_workspace(int dev, cudaStream_t s, const Need &need, Workspac
   KS_CUDA(cudaMemsetAsync(base, 0, meta, s));
   char *b = static_cast<char *>(base);
   const unsigned pending = ws.pending_error;
+  const unsigned long long launches = ws.launches;
   ws = Workspace{};
+  ws.launches = launches;
   ws.base = base;
   ws.bytes = off;
   ws.ctl = reinterpret_cast<Control *>(b + o_ctl);
@@ -383,6 +386,7 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   p.readable[1] = 0;  // buffer 1 is only written
   if (ops(dt).info(tu.variant).form == kWaveForm) KS_CUDA(ops(dt).partition_rounds(p, shape, sms, s));
   else KS_CUDA(ops(dt).partition(p, shape, grid, s));
+  ws->launches = 1;
   if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
   return KSORT_OK;
 }
@@ -468,11 +472,14 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     KS_CUDA(ops(dt).wave_handoff(p, shape, levels, true, s));
     KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
     KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+    ws->launches = 2ull * (unsigned long long)levels + 4ull;
     return KSORT_OK;
   }
   KS_CUDA(ops(dt).seed(p, tu.variant, s));
-  if (offsets || total > tu.cutoff) KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
+  const bool tiles = offsets || total > tu.cutoff;
+  if (tiles) KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
   KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+  ws->launches = tiles ? 3ull : 2ull;
   return KSORT_OK;
 }
 
@@ -710,6 +717,7 @@ ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out) {
   out->smem_levels = c.smem_levels;
   out->lookback_steps = c.lookback_steps;
   out->items_pushed = c.pushed;  // pool slots: large and small items
+  out->launches = it->second.launches;
   return KSORT_OK;
 }
 

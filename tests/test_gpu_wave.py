@@ -155,6 +155,17 @@ def test_wave_stats_and_bad_offsets(ks, restore):
     assert st["tiles"] >= st["large_items"] >= 1
     # queue entries: the small items plus large items handed to the queue
     assert st["small_items"] <= st["items_pushed"] <= st["large_items"] + st["small_items"]
+    # kernels per call as the library counts them: seed, two per wave level, hand-off,
+    # queue, finisher; the queue form: seed, tile passes, finisher; a partition: one
+    ks.ksort_set_tuning(ks.F32, wave_levels=5)
+    ks.sort_(t)
+    assert ks.ksort_get_stats()["launches"] == 2 * 5 + 4
+    ks.ksort_set_tuning(ks.F32, tile_shape=1)
+    ks.sort_(t)
+    assert ks.ksort_get_stats()["launches"] == 3
+    ks.partition_(t)
+    assert ks.ksort_get_stats()["launches"] == 1
+    ks.ksort_set_tuning(ks.F32, tile_shape=10)
     flat = _dev(gen.uniform_f32(1, 10_000))
     bad = _dev(np.array([0, 6000, 4000, 10_000], np.int64))
     ks.sort_batched_(flat, bad)
