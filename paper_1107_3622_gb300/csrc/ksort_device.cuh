@@ -105,6 +105,16 @@ __device__ __forceinline__ bool goes_left<double>(double key, double x) {
   return f64_nan(key) | f64_nan(x) | (f64_order(key) > f64_order(x));
 }
 
+// NaN test on the key's bits (integer pipes for every type; u32 keys have none).
+template <typename K>
+__device__ __forceinline__ bool key_is_nan(K) { return false; }
+template <>
+__device__ __forceinline__ bool key_is_nan<float>(float v) {
+  return (__float_as_uint(v) & 0x7fffffffu) > 0x7f800000u;
+}
+template <>
+__device__ __forceinline__ bool key_is_nan<double>(double v) { return f64_nan(v); }
+
 template <typename K>
 __device__ __forceinline__ unsigned long long key_bits(K k) {
   unsigned long long b = 0;
@@ -333,6 +343,10 @@ struct SmallShared {
 // the key of a sub-array precedes the keys equal to it (they come after it and go right),
 // and each side keeps its order. So each lane counts that index directly, with no
 // dependent chain of levels, and keys move once, to their final index.
+// The closed form needs the compare to be a total order. A run holding a NaN key runs
+// the levels themselves instead: each sub-array's lowest lane is its key, the other
+// lanes of its mask go left when !(key <= x) (one ballot), and the masks split until
+// every lane is alone; that is exact for any compare.
 // Entries of `list`: start << 8 | n << 1 | parity (parity 1: the leaf is in B).
 template <typename K>
 __device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *list, int count) {
@@ -359,18 +373,43 @@ __device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *
   const K *src = ((e & 1u) ? B : A) + s0;
   const int me = lane - lo;
   K x = K(0);
-  int pos = 0;
-  if (act) {
-    x = src[me];
+  if (act) x = src[me];
+  int dst = s0;
+  if (__any_sync(kFull, act && key_is_nan(x))) {
+    unsigned mask = act ? (((n >= 32) ? kFull : ((1u << n) - 1u)) << lo) : 0u;
+    for (int level = 0; level < 32; ++level) {  // a 32-lane sub-array needs at most 31
+      const bool big = act && (mask & (mask - 1u)) != 0u;
+      if (!__any_sync(kFull, big)) break;
+      const int piv = __ffs(mask) - 1;
+      const K key = __shfl_sync(kFull, x, piv < 0 ? 0 : piv);  // Step 1
+      const bool is_key = lane == piv;
+      const bool lf = big && !is_key && goes_left(key, x);  // Step 3
+      const unsigned low = __ballot_sync(kFull, lf) & mask;
+      if (big) {
+        const int Lc = __popc(low);
+        if (is_key) {
+          dst += Lc;  // Step 4
+          mask = 1u << lane;
+        } else if (lf) {
+          mask = low;
+        } else {
+          dst += Lc + 1;
+          mask &= ~(low | (1u << piv));
+        }
+      }
+    }
+  } else if (act) {
+    int pos = 0;
 #pragma unroll 4
     for (int j = 0; j < n; ++j) {
       const K y = src[j];
       // y < x (y goes left of key x), or y == x and y comes earlier
       pos += (goes_left(x, y) || (j < me && !goes_left(y, x))) ? 1 : 0;
     }
+    dst = s0 + pos;
   }
   __syncwarp();  // every lane has read its leaf before any key moves
-  if (act) A[s0 + pos] = x;
+  if (act) A[dst] = x;
   __syncwarp();
 }
 

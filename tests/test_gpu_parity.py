@@ -218,3 +218,23 @@ def test_f64_special_values(ref, ks, n):
             assert i == ri, (key, out_of_place)
             assert got[i:i + 1].tobytes() == a[:1].tobytes()
             assert bits(got[:i]) == bits(want[:ri]) and bits(got[i + 1:]) == bits(want[ri + 1:])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_sort_with_nan_is_a_permutation(ks, dtype):
+    """With NaN keys (Step 3's `key <= x` is false on either side of a NaN) the sort's
+    order depends on element order, so it is not compared with the oracle; it must still
+    be a permutation of its input, including inside the shared-memory leaves."""
+    rng = np.random.default_rng(12)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    for n in (2, 7, 31, 33, 1000, 5000, 100_003):
+        for frac in (0.02, 0.5):
+            a = rng.random(n).astype(npdt)
+            a[rng.random(n) < frac] = np.nan
+            got = gpu_sort(ks, a)
+            bits = np.uint32 if dtype == "f32" else np.uint64
+            assert np.array_equal(np.sort(got.view(bits)), np.sort(a.view(bits))), (n, frac)
+            # the keys that are not NaN stay in ascending order among themselves
+            fin = got[~np.isnan(got)]
+            if fin.size > 1 and np.isnan(a).sum() == 0:
+                assert np.all(fin[1:] >= fin[:-1])
