@@ -318,10 +318,14 @@ __device__ __forceinline__ bool tile_dest(long long begin, long long end, long l
 // side queued for another warp), and sides of at most kLeaf keys become leaves that
 // are finished in registers, several per warp (warp_leaf_run). Every key that reaches
 // its final index is written there in A; A is copied out at the end.
-constexpr int kLeaf = 32;
-// Queued segments are disjoint; those above kLeaf keys number at most cutoff / 33, and
-// the CTA-wide phase queues at most two leaves per partition: 1024 slots suffice for
-// cutoffs up to 16384 keys.
+#ifndef KSORT_LEAF
+#define KSORT_LEAF 32  // largest leaf (2 .. 32 keys), for sweeps
+#endif
+constexpr int kLeaf = KSORT_LEAF;
+static_assert(kLeaf >= 2 && kLeaf <= 32, "a leaf fits one warp");
+// Queued segments are disjoint; those above kLeaf keys number at most cutoff / 17 (for
+// leaves of at least 16 keys), and the CTA-wide phase queues at most two leaves per
+// partition: 1024 slots suffice for cutoffs up to 16384 keys.
 constexpr int kSmallQueue = 1024;
 constexpr int kMaxSmallCutoff = 16384;
 constexpr int kBlockSegment = 1024;
@@ -347,29 +351,23 @@ struct SmallShared {
 // the levels themselves instead: each sub-array's lowest lane is its key, the other
 // lanes of its mask go left when !(key <= x) (one ballot), and the masks split until
 // every lane is alone; that is exact for any compare.
-// Entries of `list`: start << 8 | n << 1 | parity (parity 1: the leaf is in B).
+// Entries of `list` (leaf_pack): start << 12 | first lane << 7 | n << 1 | parity (parity
+// 1: the leaf is in B); `used` = lanes the run fills.
 template <typename K>
-__device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *list, int count) {
+__device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *list, int count,
+                                              int used) {
   const int lane = threadIdx.x & 31;
   __syncwarp();
   const unsigned ent = lane < count ? list[lane] : 0u;
-  const int n_j = lane < count ? (int)((ent >> 1) & 127u) : 0;
-  int off = n_j;  // exclusive scan of leaf sizes: first lane of each leaf
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(kFull, off, o);
-    if (lane >= o) off += u;
-  }
-  off -= n_j;
-  const int used = __shfl_sync(kFull, off + n_j, count > 0 ? count - 1 : 0);
-  const unsigned starts = __reduce_or_sync(kFull, lane < count ? (1u << off) : 0u);
+  const unsigned starts =
+      __reduce_or_sync(kFull, lane < count ? (1u << ((ent >> 7) & 31u)) : 0u);
   const bool act = count > 0 && lane < used;
   const unsigned le_mask = lane == 31 ? kFull : ((2u << lane) - 1u);
   const int leaf = act ? __popc(starts & le_mask) - 1 : 0;
   const unsigned e = __shfl_sync(kFull, ent, leaf);
-  const int lo = __shfl_sync(kFull, off, leaf);
-  const int n = (int)((e >> 1) & 127u);
-  const int s0 = (int)(e >> 8);
+  const int lo = (int)((e >> 7) & 31u);
+  const int n = (int)((e >> 1) & 63u);
+  const int s0 = (int)(e >> 12);
   const K *src = ((e & 1u) ? B : A) + s0;
   const int me = lane - lo;
   K x = K(0);
@@ -416,8 +414,9 @@ __device__ __forceinline__ void warp_leaf_run(K *A, const K *B, const unsigned *
 __device__ __forceinline__ unsigned seg_pack(int s, int n, int par) {
   return ((unsigned)s << 16) | ((unsigned)n << 1) | (unsigned)par;  // s, n <= 16384
 }
-__device__ __forceinline__ unsigned leaf_pack(int s, int n, int par) {
-  return ((unsigned)s << 8) | ((unsigned)n << 1) | (unsigned)par;
+// A leaf of a run: start in its buffer, first lane in the run, size (1..32), parity.
+__device__ __forceinline__ unsigned leaf_pack(int s, int n, int par, int lane0) {
+  return ((unsigned)s << 12) | ((unsigned)lane0 << 7) | ((unsigned)n << 1) | (unsigned)par;
 }
 
 // Lane 0 queues a segment.
@@ -565,8 +564,8 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
 
   if (m <= kLeaf) {
     if (warp == 0) {
-      if (lane == 0) leaves[0] = leaf_pack(0, m, 0);
-      warp_leaf_run(A, B, leaves, 1);
+      if (lane == 0) leaves[0] = leaf_pack(0, m, 0, 0);
+      warp_leaf_run(A, B, leaves, 1, m);
     }
     nseg = 1;
   } else {
@@ -611,10 +610,10 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
       while (true) {
         if (n <= kLeaf) {  // a leaf (queued by the CTA-wide phase)
           if (nlanes + n > 32) {
-            warp_leaf_run(A, B, leaves, nleaves);
+            warp_leaf_run(A, B, leaves, nleaves, nlanes);
             nleaves = nlanes = 0;
           }
-          if (lane == 0) leaves[nleaves] = leaf_pack(s, n, par);
+          if (lane == 0) leaves[nleaves] = leaf_pack(s, n, par, nlanes);
           ++nleaves;
           nlanes += n;
           break;
@@ -635,10 +634,10 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
           const int cs = c ? rs : ls, cn = c ? rn : ln;
           if (cn >= 2 && cn <= kLeaf) {
             if (nlanes + cn > 32) {
-              warp_leaf_run(A, B, leaves, nleaves);
+              warp_leaf_run(A, B, leaves, nleaves, nlanes);
               nleaves = nlanes = 0;
             }
-            if (lane == 0) leaves[nleaves] = leaf_pack(cs, cn, cp);
+            if (lane == 0) leaves[nleaves] = leaf_pack(cs, cn, cp, nlanes);
             ++nleaves;
             nlanes += cn;
           }
@@ -664,7 +663,7 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
         atomicSub(&q.pending, 1);
       }
     }
-    if (nleaves) warp_leaf_run(A, B, leaves, nleaves);
+    if (nleaves) warp_leaf_run(A, B, leaves, nleaves, nlanes);
   }
   bsync();
   copy_out_v<K, kSmallThreads>(A, out, (unsigned)m, tid);
