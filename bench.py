@@ -281,6 +281,27 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo where it has one)."""
+    import platform
+    arm = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k = k.strip().lower()
+                if k in ("model name", "cpu model", "processor name"):
+                    return v.strip()
+                if k in ("cpu implementer", "cpu part") and k not in arm:
+                    arm[k] = v.strip()
+    except OSError:
+        pass
+    if arm:  # Arm cores name themselves by implementer and part number
+        return (f"{platform.machine()} implementer {arm.get('cpu implementer', '?')} "
+                f"part {arm.get('cpu part', '?')}")
+    return platform.machine()
+
+
 def cpu_baseline(n: int, budget_s: float, seed: int):
     """The oracle as it stands, one thread, on `n`-key float32 arrays, repeated until
     the budget is used (at least once). Returns (keys/s, sample text, seconds)."""
@@ -403,6 +424,7 @@ def run_ours(args, dist: Dist):
                    "l2": "flushed before every step (256 MiB write), input restored by an "
                          "untimed device copy; per-step CUDA events around ksort_sort",
                    "vs_baseline_ref": "Table 1 K-sort 3.2892 s at n=7e6 (paper's CPU)",
+                   "device_l2_bytes": int(torch.cuda.get_device_properties(0).L2_cache_size),
                    "tuning": tuning},
         "roofline": roofline,
         "e2e": e2e,
@@ -430,7 +452,8 @@ def run_ours(args, dist: Dist):
             v, sample, spent = cpu_baseline(min(n, N_KEYS), args.cpu_seconds, None)
             line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1,
                                     "kind": "oracle", "sample": sample,
-                                    "seconds": round(spent, 2), "host_cpus": os.cpu_count()}
+                                    "seconds": round(spent, 2), "host_cpus": os.cpu_count(),
+                                    "cpu_model": cpu_model()}
     return line
 
 
@@ -692,7 +715,7 @@ def run_sweep(args):
         ks.ksort_reserve_workspace(code, max(gen.TABLE1_SIZES), 1)
         for si, n in enumerate(gen.TABLE1_SIZES):
             cfg = 1 if name == "f32" else 2
-            ms, algo = [], []
+            ms, algo, passes = [], [], []
             for r in range(reps):
                 if args.sweep_pattern == "uniform":
                     keys = gen.uniform_torch(name, gen.seed_for(cfg, si, r), n, device="cuda")
@@ -712,6 +735,7 @@ def run_sweep(args):
                 ms.append(e0.elapsed_time(e1))
                 st = ks.ksort_get_stats()
                 algo.append(2 * kb * (st["large_keys"] + st["small_keys"]))
+                passes.append(st["large_keys"] / n)
                 if not bool((keys[1:] >= keys[:-1]).all()):
                     raise RuntimeError(f"unsorted output at n={n} {name} rep {r}")
             if ks.ksort_get_device_error():
@@ -722,6 +746,9 @@ def run_sweep(args):
                    "min_ms": round(min(ms), 4), "keys_per_s": round(n / (mean_ms / 1e3), 1),
                    "algorithmic_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
                    "lower_bound_frac": round(2 * kb * n / (mean_ms / 1e3) / 1e9 / peak, 5),
+                   # tile passes a key goes through on average (large_keys / n): the
+                   # number of global partition levels, counted by the library
+                   "tile_levels": round(statistics.fmean(passes), 2),
                    "paper_table1_s": PAPER_TABLE1_S[n]}
             if args.sweep_oracle_reps > 0:
                 t = []

@@ -120,7 +120,7 @@ def test_sort_uniform(ref, ks, dtype, n):
 @pytest.mark.parametrize("dtype", ["f32", "u32"])
 @pytest.mark.parametrize("pattern", ["sorted", "reverse", "distinct16", "organ_pipe",
                                      "quantized15"])
-@pytest.mark.parametrize("n", [20_000, 50_000])
+@pytest.mark.parametrize("n", [20_000, 30_000, 50_000])
 def test_sort_stress(ref, ks, dtype, pattern, n):
     """Input-structure stress at oracle-feasible sizes: the paper's worst cases for the
     first-element key (Section 1; O(n^2) on sorted input)."""
