@@ -441,6 +441,8 @@ def run_ours(args, dist: Dist):
     if dist.rank == 0:
         if "partition" in extras:
             line["partition_pass"] = run_partition_pass(ks, n, peak, peak_src, args)
+            # the same at a size far beyond L2, where HBM is the bound
+            line["partition_pass_5e7"] = run_partition_pass(ks, 50_000_000, peak, peak_src, args)
         if "exact" in extras:
             line["exact_partition"] = run_exact_partition(ks, n, peak, peak_src)
         if "batched" in extras:
@@ -486,8 +488,8 @@ def run_e2e(ks, host, args, stream):
 
 
 def run_partition_pass(ks, n, peak, peak_src, args):
-    """ksort_partition_out alone (autotuned form): rotating over 8 input/output pairs
-    (> L2 in total)."""
+    """ksort_partition_out alone (autotuned form): rotating over input/output pairs that
+    are larger than L2 in total (8 pairs, or 2 for arrays beyond 2e7 keys)."""
     import torch
     from paper_1107_3622_gb300 import autotune
     saved = ks.ksort_get_tuning(ks.F32)
@@ -502,7 +504,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     nt, ipt, _ = ks.ksort_tile_shape(ks.F32, ks.ksort_get_tuning(ks.F32)["tile_shape"])
     kname = f"part_kernel<{nt}x{ipt}>"
     ks.ksort_reserve_workspace(ks.F32, n, 1)
-    R, reps = 8, 20
+    R, reps = (8, 20) if n < 20_000_000 else (2, 10)
     ins = [torch.from_numpy(gen.uniform_f32(gen.seed_for(1, 6, 500 + r), n)).cuda()
            for r in range(R)]
     outs = [torch.empty_like(x) for x in ins]
