@@ -537,7 +537,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),
             "peak_source": f"{peak_src} hbm_gbs",
             "traffic": recorded_traffic(f"ksort_partition_out<float> {kname}",
-                                        f"n={n} f32 rotating 8 buffers"),
+                                        f"n={n} f32 rotating {R} buffers"),
             "algorithmic_bytes_per_launch": 8 * n,
             "method": f"{R} buffer pairs ({2 * R * 4 * n >> 20} MiB) rotated, {reps} rounds, "
                       "CUDA events around back-to-back launches"}
