@@ -10,10 +10,16 @@
 // contents of the two sides are those of Steps 1-4, the order inside each side is the
 // tile order documented at tile_kernel.
 //
-// Kernels, in stream order: seed_kernel (one CTA) starts a generation and queues the
-// roots; tile_kernel (phase 1) runs every tile pass of the sub-arrays above the
+// Kernels of a sort, in stream order: seed_kernel (one CTA) starts a generation and
+// queues the roots; tile_kernel (phase 1; or its staged and warp-role forms,
+// tile_pipe_kernel and tile_ws_kernel) runs every tile pass of the sub-arrays above the
 // cutoff, queuing sides as sub-arrays complete, until all of them are done;
-// small_kernel (phase 2) finishes the queued small sub-arrays in shared memory.
+// small_kernel (phase 2) finishes the queued small sub-arrays in shared memory. The
+// wave form runs the upper levels first as wave_count_kernel / wave_scatter_kernel
+// pairs, one per level, and hands what remains to tile_kernel with wave_handoff_kernel.
+// Single partitions: part_kernel (one launch), part_round_kernel (the wave form's,
+// cooperative), exact_*_kernel (the paper's element order), and tile_kernel for the
+// fixed-scratch entry point.
 #pragma once
 
 #include <cstdint>
