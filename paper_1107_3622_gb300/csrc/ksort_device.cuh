@@ -140,6 +140,18 @@ __device__ __forceinline__ void raise_error(Control *ctl, unsigned code, unsigne
   atomicExch(&ctl->abort, 1u);
 }
 
+// Every sub-array the kernels record (work items, wave lists) is checked here when it is
+// created: inside the caller's buffer and within one partition's size. Records are
+// only ever read back, so every range a kernel derives from one (tiles, bulk copies,
+// destinations) stays inside the buffers; a violation is reported and not recorded.
+// This stands in for a memory checker, which this GPU pool does not offer.
+__device__ __forceinline__ bool sub_array_ok(const SortParams &p, long long b, long long e,
+                                             unsigned long long where) {
+  if (b >= 0 && b < e && e <= p.total && e - b <= kMaxItemKeys) return true;
+  raise_error(p.ctl, kDevInternal, 0xF00000000ull | where);
+  return false;
+}
+
 // ----------------------------------------------------------------------------- tiles
 // Tile grid of a sub-array [begin, end) in buffer `buf`: the first classified element
 // is begin + 1 (begin holds the key); tiles are anchored at the 16-byte boundary at or
@@ -703,6 +715,7 @@ __device__ __forceinline__ unsigned long long reserve_item(const SortParams &p, 
                                                            unsigned *tiles_out) {
   Control *ctl = p.ctl;
   *tiles_out = 0;
+  if (!sub_array_ok(p, b, e, 1)) return 0;
   const long long m = e - b;
   const K *buf = (flags & kItemScratch) ? static_cast<const K *>(p.scratch)
                                         : static_cast<const K *>(p.keys);
@@ -2772,7 +2785,9 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) wave_scatter_kernel(S
 #pragma unroll
         for (int c = 0; c < 2; ++c) {  // Steps 5-6
           const long long mm = ce[c] - cb[c];
-          if (mm > p.cutoff) {
+          if (mm > p.cutoff && !sub_array_ok(p, cb[c], ce[c], 3)) {
+            // reported, not recorded
+          } else if (mm > p.cutoff) {
             const unsigned long long old = atomicAdd(
                 &ctl->wave_ctr[(level + 1) & 1], (1ull << kWaveKeyBits) | (unsigned long long)(mm - 1));
             const unsigned long long idx = old >> kWaveKeyBits;
@@ -3173,6 +3188,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(SortParams p) {
 // Wave form: a root above the cutoff goes on the level-0 list (true), else false.
 __device__ __forceinline__ bool seed_wave_root(const SortParams &p, long long b, long long e) {
   if (!p.wave || e - b <= p.cutoff || (p.root_flags & kItemPartitionOnly)) return false;
+  if (!sub_array_ok(p, b, e, 2)) return true;  // reported, not recorded
   Control *ctl = p.ctl;
   const unsigned long long old = atomicAdd(
       &ctl->wave_ctr[0], (1ull << kWaveKeyBits) | (unsigned long long)(e - b - 1));
