@@ -181,6 +181,10 @@ KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *o
  *   wave_levels:   forms 10 .. 12 only: recursion levels run as level-synchronous
  *                  passes before the work queue takes over (1 .. 64); -1 = automatic
  *                  (about log2 of the mean array length over the cutoff, plus 2).
+ *   medium_tiles:  forms 1 .. 3 and 10 .. 12 (the register form's work queue): a
+ *                  sub-array of 2 .. medium_tiles tile passes is taken by one CTA, which
+ *                  counts every tile first and then moves them with the prefixes it
+ *                  knows (no look-back); 1 .. 16, -1 = off (the default).
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
@@ -188,6 +192,7 @@ typedef struct {
     int32_t spin_limit_ms;
     int32_t tile_shape;
     int32_t wave_levels;
+    int32_t medium_tiles;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);

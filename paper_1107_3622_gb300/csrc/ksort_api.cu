@@ -75,12 +75,14 @@ struct Tuning {
   int spin_limit_ms;
   int variant;      // tile shape of the tile passes, 0 .. kTileVariants - 1
   int wave_levels;  // wave form: level-synchronous levels; 0: automatic
+  int medium_tiles; // register-form queue: largest item one CTA takes whole; 0: off
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0}, {2048, 0, 2000, 0, 0}, {4096, 0, 2000, 0, 0}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0}, {2048, 0, 2000, 0, 0, 0},
+                      {4096, 0, 2000, 0, 0, 0}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -451,6 +453,11 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
   }
   SortParams p = sort_params(*ws, keys, tu);
   p.offsets = reinterpret_cast<const long long *>(offsets);
+  {
+    // medium items are served by tile_kernel alone (the register form's queue)
+    const int form = ops(dt).info(tu.variant).form;
+    p.medium_tiles = form == 0 || form == kWaveForm ? tu.medium_tiles : 0;
+  }
   p.num_roots = offsets ? num_arrays : 1;
   p.total = total;
   p.readable[0] = total;
@@ -753,6 +760,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
     return KSORT_ERR_INVALID_ARG;
   if (t->tile_shape < 0 || t->tile_shape > kTileVariants) return KSORT_ERR_INVALID_ARG;
   if (t->wave_levels < -1 || t->wave_levels > 64) return KSORT_ERR_INVALID_ARG;
+  if (t->medium_tiles < -1 || t->medium_tiles > kMediumMaxTiles) return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
@@ -760,6 +768,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->spin_limit_ms) g.spin_limit_ms = t->spin_limit_ms;
   if (t->tile_shape) g.variant = t->tile_shape - 1;
   if (t->wave_levels) g.wave_levels = t->wave_levels < 0 ? 0 : t->wave_levels;
+  if (t->medium_tiles) g.medium_tiles = t->medium_tiles < 0 ? 0 : t->medium_tiles;
   return KSORT_OK;
 }
 
@@ -773,6 +782,7 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->spin_limit_ms = g.spin_limit_ms;
   out->tile_shape = g.variant + 1;
   out->wave_levels = g.wave_levels ? g.wave_levels : -1;
+  out->medium_tiles = g.medium_tiles ? g.medium_tiles : -1;
   return KSORT_OK;
 }
 

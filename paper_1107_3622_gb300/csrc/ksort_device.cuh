@@ -721,10 +721,13 @@ __device__ __forceinline__ unsigned long long reserve_item(const SortParams &p, 
                                         : static_cast<const K *>(p.keys);
   const bool small = m <= p.cutoff && !(flags & kItemPartitionOnly);
   const unsigned tiles = small ? 1u : tile_count<K, TILE>(buf, b, e);
+  // a medium item takes one ticket; its CTA runs all of its tile passes
+  const bool medium = !small && tiles >= 2 && (int)tiles <= p.medium_tiles;
+  const unsigned tickets = medium ? 1u : tiles;
   unsigned long long t0 = 0;
   if (!small) {
-    t0 = atomicAdd(&ctl->lb_used, (unsigned long long)tiles);
-    if (t0 + tiles > p.lb_cap) {
+    t0 = atomicAdd(&ctl->lb_used, (unsigned long long)tickets);
+    if (t0 + tickets > p.lb_cap) {
       raise_error(ctl, kDevWorkspaceExhausted, 2);
       return 0;
     }
@@ -740,7 +743,7 @@ __device__ __forceinline__ unsigned long long reserve_item(const SortParams &p, 
   it->key = key_bits<K>(__ldcg(buf + b));
   it->tiles = tiles;
   it->lb = (unsigned)t0;
-  it->flags = flags | (small ? kItemSmall : 0u);
+  it->flags = flags | (small ? kItemSmall : 0u) | (medium ? kItemMedium : 0u);
   it->epoch = epoch;
   if (small) {
     __threadfence();
@@ -753,7 +756,7 @@ __device__ __forceinline__ unsigned long long reserve_item(const SortParams &p, 
     atomicAdd(&ctl->large_pushed, 1ull);  // before any ticket can be served
     __threadfence();
     *t0_out = t0;
-    *tiles_out = tiles;
+    *tiles_out = tickets;
   }
   return idx;
 }
@@ -875,7 +878,92 @@ struct TileCtaShared {
   unsigned long long k;  // ticket
   unsigned long long cidx[2], ct0[2];
   unsigned ctiles[2];
+  unsigned long long c_less;  // #{x < key} of the item being finished
+  unsigned mL[kMediumMaxTiles], mG[kMediumMaxTiles];  // a medium item's tile counts
 };
+
+// Keys [vlo, vhi) of the tile at src + lo (16-byte aligned) into registers; thread i
+// holds tile positions (v * NT + i) * VEC + l. Whole vectors inside the range move
+// with 128-bit loads, the edges one key at a time; nothing outside the range is read.
+template <typename K, int NT, int IPT>
+__device__ __forceinline__ void tile_load(const K *src, long long lo, int vlo, int vhi,
+                                          K (&x)[IPT]) {
+  constexpr int VEC = Vec<K>::N, NV = IPT / VEC;
+  using V = typename Vec<K>::T;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int k0 = (v * NT + (int)threadIdx.x) * VEC;
+    if (k0 >= vlo && k0 + VEC <= vhi) {
+      const V q = __ldcg(reinterpret_cast<const V *>(src + lo + k0));
+      if constexpr (VEC == 4) {
+        x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
+      } else {
+        x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < VEC; ++l) {
+        const int k = k0 + l;
+        x[v * VEC + l] = (k >= vlo && k < vhi) ? __ldcg(src + lo + k) : K(0);
+      }
+    }
+  }
+}
+
+// Whole CTA, once every tile pass of item h is written and c = #{x < key} is known:
+// Step 4 (the key to its final index) and Steps 5-6 (both sides queued; the tickets of
+// large sides published by every thread), then the item counts as completed.
+template <typename K, int TILE, int NW>
+__device__ __forceinline__ void finish_item(const SortParams &p, unsigned epoch, const Item &it,
+                                            long long h, unsigned long long c,
+                                            TileCtaShared<NW> &sh, unsigned long long &st_large,
+                                            unsigned long long &st_large_keys) {
+  const int tid = threadIdx.x;
+  Control *ctl = p.ctl;
+  K *const buf0 = static_cast<K *>(p.keys);
+  const unsigned par = it.flags & kItemScratch;
+  K *dst = static_cast<K *>(par ? p.keys : p.scratch);
+  const K key = bits_key<K>(it.key);
+  if (tid == 0) {
+    sh.ctiles[0] = sh.ctiles[1] = 0;
+    const long long kpos = it.begin + (long long)c;
+    if (kpos >= it.end) {
+      raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)h);
+    } else if (it.flags & kItemPartitionOnly) {
+      dst[kpos] = key;  // a single partition: the key index is the result
+      if (p.key_index) *p.key_index = (long long)c;
+    } else {
+      buf0[kpos] = key;  // Step 4
+      const unsigned cflags = par ^ kItemScratch;
+      const long long cb[2] = {it.begin, kpos + 1};
+      const long long ce[2] = {kpos, it.end};
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {  // Steps 5-6
+        const long long mm = ce[s] - cb[s];
+        if (mm == 1) {
+          if (cflags & kItemScratch) buf0[cb[s]] = __ldcg(dst + cb[s]);
+        } else if (mm >= 2) {
+          unsigned long long t0 = 0;
+          unsigned tiles = 0;
+          sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb[s], ce[s], cflags, &t0, &tiles);
+          sh.ct0[s] = t0;
+          sh.ctiles[s] = tiles;
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+    if (sh.ctiles[s]) publish_tickets(p, epoch, sh.cidx[s], sh.ct0[s], sh.ctiles[s], tid, blockDim.x);
+  __syncthreads();
+  if (tid == 0) {
+    ++st_large;
+    st_large_keys += (unsigned long long)(it.end - it.begin);
+    __threadfence();
+    atomicAdd(&ctl->large_completed, 1ull);
+  }
+}
 
 template <typename K, int NT, int IPT>
 __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParams p) {
@@ -933,6 +1021,114 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
     }
     __syncthreads();
     if (sh.r <= 0) break;
+    if (sh.it.flags & kItemMedium) {
+      // ---- a medium item: this CTA runs all its tile passes, counting first and then
+      // moving, so each tile's prefix is known locally (no look-back, one ticket)
+      const Item it = sh.it;
+      const long long h = sh.h;
+      const unsigned par = it.flags & kItemScratch;
+      const K *src = par ? buf1 : buf0;
+      K *dst = par ? buf0 : buf1;
+      const K key = bits_key<K>(it.key);  // Step 1
+      const long long base = tile_base(src, it.begin), first = it.begin + 1;
+      const unsigned T = it.tiles;
+      if (tid < kMediumMaxTiles) {
+        sh.mL[tid] = 0;
+        sh.mG[tid] = 0;
+      }
+      __syncthreads();
+      for (unsigned t = 0; t < T; ++t) {  // Step 3: counts of every tile
+        const long long lo = base + (long long)t * TILE;
+        const int vlo = (int)(first > lo ? first - lo : 0);
+        const int vhi = (int)(it.end - lo < TILE ? it.end - lo : TILE);
+        K x[IPT];
+        tile_load<K, NT, IPT>(src, lo, vlo, vhi, x);
+        unsigned cl = 0, cg = 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+#pragma unroll
+          for (int l = 0; l < VEC; ++l) {
+            const int k = (v * NT + tid) * VEC + l;
+            if (k >= vlo && k < vhi) {
+              if (goes_left(key, x[v * VEC + l])) ++cl;
+              else ++cg;
+            }
+          }
+        }
+        cl = __reduce_add_sync(kFull, cl);
+        cg = __reduce_add_sync(kFull, cg);
+        if (lane == 0) {
+          atomicAdd(&sh.mL[t], cl);
+          atomicAdd(&sh.mG[t], cg);
+        }
+      }
+      __syncthreads();
+      unsigned long long E = 0;
+      bool bad = false;
+      for (unsigned t = 0; t < T && !bad; ++t) {  // Steps 3.1/3.2 per tile, prefix known
+        const long long lo = base + (long long)t * TILE;
+        const int vlo = (int)(first > lo ? first - lo : 0);
+        const int vhi = (int)(it.end - lo < TILE ? it.end - lo : TILE);
+        K x[IPT];
+        tile_load<K, NT, IPT>(src, lo, vlo, vhi, x);
+        unsigned lessbits = 0, gebits = 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+#pragma unroll
+          for (int l = 0; l < VEC; ++l) {
+            const int j = v * VEC + l, k = (v * NT + tid) * VEC + l;
+            const bool valid = k >= vlo && k < vhi;
+            const bool le = goes_left(key, x[j]);
+            lessbits |= (unsigned)(valid && le) << j;
+            gebits |= (unsigned)(valid && !le) << j;
+          }
+        }
+        const unsigned mine = (unsigned)__popc(lessbits) | ((unsigned)__popc(gebits) << 16);
+        unsigned incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned u = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += u;
+        }
+        if (lane == 31) {
+          sh.wl[w] = incl & 0xffffu;
+          sh.wg[w] = incl >> 16;
+        }
+        __syncthreads();
+        unsigned L = 0, G = 0, wlx = 0, wgx = 0;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) {
+          const unsigned a = sh.wl[i], b = sh.wg[i];
+          if (i < w) {
+            wlx += a;
+            wgx += b;
+          }
+          L += a;
+          G += b;
+        }
+        scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
+        __syncthreads();
+        long long lbase = 0, gbase = 0;
+        if (L != sh.mL[t] || G != sh.mG[t] ||
+            !tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase)) {
+          if (tid == 0) raise_error(ctl, kDevInternal, 0x500000000ull | t);
+          bad = true;  // uniform: every thread computed the same values
+        } else {
+          copy_out_v<K, NT>(sout, dst + lbase, L, tid);
+          copy_out_v<K, NT>(sout + L, dst + gbase, G, tid);
+          E += L;
+        }
+        __syncthreads();  // sout and the warp counts are reused by the next tile
+      }
+      if (bad) break;
+      if (tid == 0) {
+        k_next = atomicAdd(&ctl->tq_head, 1ull);
+        st_tiles += T;
+      }
+      finish_item<K, TILE, NW>(p, epoch, it, h, E, sh, st_large, st_large_keys);
+      if (tid == 0) trace_mark(p, sh.k, 6);  // completed
+      continue;
+    }
     const Item it = sh.it;
     const unsigned t = sh.t;
     const long long lo = sh.lo, h = sh.h;
@@ -1055,50 +1251,13 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);
       k_next = atomicAdd(&ctl->tq_head, 1ull);  // the next ticket (its claim overlaps)
       sh.last = done_before == it.tiles - 1;
-      sh.ctiles[0] = sh.ctiles[1] = 0;
       if (sh.last) {
         __threadfence();
-        const unsigned long long c = ld_acquire(&p.ictl[h].less);
-        const long long kpos = it.begin + (long long)c;
-        if (kpos >= it.end) {
-          raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)h);
-        } else if (it.flags & kItemPartitionOnly) {
-          dst[kpos] = key;  // a single partition: the key index is the result
-          if (p.key_index) *p.key_index = (long long)c;
-        } else {
-          buf0[kpos] = key;  // Step 4
-          const unsigned cflags = par ^ kItemScratch;
-          const long long cb[2] = {it.begin, kpos + 1};
-          const long long ce[2] = {kpos, it.end};
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {  // Steps 5-6
-            const long long mm = ce[s] - cb[s];
-            if (mm == 1) {
-              if (cflags & kItemScratch) buf0[cb[s]] = __ldcg(dst + cb[s]);
-            } else if (mm >= 2) {
-              unsigned long long t0 = 0;
-              unsigned tiles = 0;
-              sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb[s], ce[s], cflags, &t0, &tiles);
-              sh.ct0[s] = t0;
-              sh.ctiles[s] = tiles;
-            }
-          }
-        }
+        sh.c_less = ld_acquire(&p.ictl[h].less);
       }
     }
     __syncthreads();
-    if (sh.last) {
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-        if (sh.ctiles[s]) publish_tickets(p, epoch, sh.cidx[s], sh.ct0[s], sh.ctiles[s], tid, NT);
-      __syncthreads();
-      if (tid == 0) {
-        ++st_large;
-        st_large_keys += (unsigned long long)(it.end - it.begin);
-        __threadfence();
-        atomicAdd(&ctl->large_completed, 1ull);
-      }
-    }
+    if (sh.last) finish_item<K, TILE, NW>(p, epoch, it, h, sh.c_less, sh, st_large, st_large_keys);
     if (tid == 0) trace_mark(p, sh.k, 6);  // completed
   }
   if (tid == 0) {

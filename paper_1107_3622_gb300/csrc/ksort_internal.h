@@ -23,7 +23,11 @@ enum : unsigned {
   kItemScratch = 1u,        // keys of the item live in buffer 1 (else in buffer 0)
   kItemSmall = 2u,          // finished in shared memory by one CTA
   kItemPartitionOnly = 4u,  // Steps 1-4 only: key and sides go to buffer 1, no recursion
+  kItemMedium = 8u,         // one ticket: a single CTA runs every tile pass of the item
 };
+
+// Largest item (in tile passes) that may go to a single CTA (kItemMedium).
+constexpr int kMediumMaxTiles = 16;
 
 // Largest sub-array, in keys, that one partition may handle: tile prefixes are
 // carried in 31 bits of a look-back descriptor.
@@ -114,6 +118,7 @@ struct SortParams {
   unsigned long long *wave_cnt;
   unsigned long long *wave_fin;
   int wave;                  // nonzero: the seed queues large roots on the level-0 list
+  int medium_tiles;          // items of 2 .. medium_tiles tile passes go to one CTA; 0: off
 };
 constexpr int kTraceWords = 8;
 

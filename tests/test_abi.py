@@ -115,6 +115,13 @@ def test_tile_shapes_and_tuning_fields(lib):
         for bad in (-2, 65):
             with pytest.raises(ks.KSortError):
                 ks.ksort_set_tuning(code, wave_levels=bad)
+        assert before["medium_tiles"] == -1 or before["medium_tiles"] in range(1, 17)
+        for bad in (-2, 17):
+            with pytest.raises(ks.KSortError):
+                ks.ksort_set_tuning(code, medium_tiles=bad)
+        ks.ksort_set_tuning(code, medium_tiles=5)
+        assert ks.ksort_get_tuning(code)["medium_tiles"] == 5
+        ks.ksort_set_tuning(code, medium_tiles=before["medium_tiles"])
         ks.ksort_set_tuning(code, tile_shape=2)
         nt, ipt, _ = shapes[1]
         assert ks.ksort_tile_keys(code) == nt * ipt
