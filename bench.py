@@ -84,7 +84,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the library's default tuning instead of the autotuned one")
     ap.add_argument("--tile-shape", type=int, default=0,
-                    help="fixed form of the partition passes (1..9) instead of autotuning")
+                    help="fixed form of the partition passes (1..12) instead of autotuning")
     ap.add_argument("--cutoff", type=int, default=0,
                     help="fixed shared-memory cutoff instead of autotuning")
     ap.add_argument("--serving-requests", type=int, default=10_000,
@@ -501,8 +501,11 @@ def run_partition_pass(ks, n, peak, peak_src, args):
         tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
                      keys_per_thread=shape[1], form=shape[2], search_ms=e["ms"],
                      cached=e["cached"])
-    nt, ipt, _ = ks.ksort_tile_shape(ks.F32, ks.ksort_get_tuning(ks.F32)["tile_shape"])
-    kname = f"part_kernel<{nt}x{ipt}>"
+    nt, ipt, form = ks.ksort_tile_shape(ks.F32, ks.ksort_get_tuning(ks.F32)["tile_shape"])
+    if form == 3:  # the wave form's split partition: count, then move
+        kname, launches = f"split_count_kernel + split_move_kernel<{nt}x{ipt}>", "two launches"
+    else:
+        kname, launches = f"part_kernel<{nt}x{ipt}>", "one launch"
     ks.ksort_reserve_workspace(ks.F32, n, 1)
     R, reps = (8, 20) if n < 20_000_000 else (2, 10)
     ins = [torch.from_numpy(gen.uniform_f32(gen.seed_for(1, 6, 500 + r), n)).cuda()
@@ -531,7 +534,7 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
                         tile_shape=saved["tile_shape"],
                         wave_levels=saved.get("wave_levels", -1))
-    return {"kernel": f"ksort_partition_out: {kname} <float>, one launch",
+    return {"kernel": f"ksort_partition_out: {kname} <float>, {launches}",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
             "achieved_gbs": round(gbs, 1), "peak": peak, "frac": round(gbs / peak, 4),

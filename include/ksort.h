@@ -71,11 +71,15 @@ KSORT_API ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, in
                                int64_t *key_index_dev, ksort_stream_t stream);
 
 /* The same partition, out of place: in_dev is read, out_dev (n keys, not overlapping
- * in_dev) receives the partitioned keys. One launch, one read and one write pass over the
- * keys: CTAs take the tiles round-robin, stage each next tile into shared memory by a
- * bulk copy, chain the tiles' less counts by decoupled look-back, and write each tile's
- * two sides to the front and the back of out_dev. The CTA shape is that of the tuned
- * tile_shape (see ksort_set_tuning). */
+ * in_dev) receives the partitioned keys. Tile shapes 1-9: one launch, one read and one
+ * write pass over the keys: CTAs take the tiles round-robin, stage each next tile into
+ * shared memory by a bulk copy, chain the tiles' less counts by decoupled look-back, and
+ * write each tile's two sides to the front and the back of out_dev. Tile shapes 10-12
+ * (the wave form): two launches with no waits between CTAs: every warp counts the less
+ * keys of its run of warp tiles, then (under programmatic dependent launch) moves them
+ * with the prefix of those counts; the keys are read twice. The CTA shape is that of the
+ * tuned tile_shape (see ksort_set_tuning); the order within each side differs between
+ * forms, the key index and the two sides' contents do not. */
 KSORT_API ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
                                    int64_t n, int64_t *key_index_dev, ksort_stream_t stream);
 
@@ -215,7 +219,7 @@ KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
  *                     sub-arrays of one depth are partitioned by two launches, one
  *                     counting and one moving keys, over equal spans of their keys per
  *                     CTA, with no waits between CTAs; the remaining levels then run as
- *                     form 0. Single partitions (ksort_partition*) use the CTA shape only. */
+ *                     form 0. Single partitions: see ksort_partition_out. */
 KSORT_API ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
                                           int32_t *keys_per_thread, int32_t *form);
 

@@ -209,8 +209,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
     best_ms = measure(best)
     axes = (("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS), ("cutoff", cutoffs),
             ("ctas_per_sm", FINISHER_CTAS))
-    if kind == "partition":  # one part_kernel launch: only its CTA shape matters
-        axes = (("tile_shape", SHAPES[:3]),)
+    if kind == "partition":  # part_kernel or the split pair: only the CTA shape matters
+        axes = (("tile_shape", SHAPES[:3] + WAVE_SHAPES),)
     for _ in range(max_rounds):
         improved = False
         for name, values in axes:

@@ -50,7 +50,7 @@ struct Ops {
   cudaError_t (*wave_occupancy)(int, int *);
   cudaError_t (*wave_level)(const SortParams &, int, int, int, bool, cudaStream_t);
   cudaError_t (*wave_handoff)(const SortParams &, int, int, bool, cudaStream_t);
-  cudaError_t (*partition_rounds)(const SortParams &, int, int, cudaStream_t);
+  cudaError_t (*partition_split)(const SortParams &, int, int, cudaStream_t);
 };
 
 template <typename K>
@@ -60,7 +60,7 @@ Ops ops_for() {
              &Launcher<K>::tile_count, &Launcher<K>::part_occupancy,   &Launcher<K>::partition,
              &Launcher<K>::exact_work_bytes, &Launcher<K>::exact,
              &Launcher<K>::wave_occupancy, &Launcher<K>::wave_level, &Launcher<K>::wave_handoff,
-             &Launcher<K>::partition_rounds};
+             &Launcher<K>::partition_split};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -368,8 +368,9 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
     if (!in_place) KS_CUDA(cudaMemcpyAsync(dst, in, kb, cudaMemcpyDeviceToDevice, s));
     return KSORT_OK;
   }
-  // One launch of part_kernel (the CTA shape of the tuned form), or of part_round_kernel
-  // for the wave form: buffer 0 is read, buffer 1 receives the result.
+  // One launch of part_kernel (the CTA shape of the tuned form), or for the wave form the
+  // count and move launches of the split partition: buffer 0 is read, buffer 1 receives
+  // the result.
   const int shape = tu.variant % kTileShapes;
   const long long tiles = ops(dt).tile_count(shape, in, 0, n);  // form-0 variants: plain tiles
   if ((unsigned long long)tiles > ws->lb_cap) return KSORT_ERR_INVALID_ARG;
@@ -386,9 +387,13 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   p.key_index = reinterpret_cast<long long *>(key_index);
   p.readable[0] = n;
   p.readable[1] = 0;  // buffer 1 is only written
-  if (ops(dt).info(tu.variant).form == kWaveForm) KS_CUDA(ops(dt).partition_rounds(p, shape, sms, s));
-  else KS_CUDA(ops(dt).partition(p, shape, grid, s));
-  ws->launches = 1;
+  if (ops(dt).info(tu.variant).form == kWaveForm) {
+    KS_CUDA(ops(dt).partition_split(p, shape, sms, s));
+    ws->launches = 2;
+  } else {
+    KS_CUDA(ops(dt).partition(p, shape, grid, s));
+    ws->launches = 1;
+  }
   if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
   return KSORT_OK;
 }

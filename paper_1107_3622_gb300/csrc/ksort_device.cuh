@@ -17,9 +17,9 @@
 // small_kernel (phase 2) finishes the queued small sub-arrays in shared memory. The
 // wave form runs the upper levels first as wave_count_kernel / wave_scatter_kernel
 // pairs, one per level, and hands what remains to tile_kernel with wave_handoff_kernel.
-// Single partitions: part_kernel (one launch), part_round_kernel (the wave form's,
-// cooperative), exact_*_kernel (the paper's element order), and tile_kernel for the
-// fixed-scratch entry point.
+// Single partitions: part_kernel (one launch), split_count_kernel / split_move_kernel
+// (the wave form's: count, then move, no waits between CTAs), exact_*_kernel (the
+// paper's element order), and tile_kernel for the fixed-scratch entry point.
 #pragma once
 
 #include <cstdint>
@@ -882,17 +882,18 @@ struct TileCtaShared {
   unsigned mL[kMediumMaxTiles], mG[kMediumMaxTiles];  // a medium item's tile counts
 };
 
-// Keys [vlo, vhi) of the tile at src + lo (16-byte aligned) into registers; thread i
-// holds tile positions (v * NT + i) * VEC + l. Whole vectors inside the range move
-// with 128-bit loads, the edges one key at a time; nothing outside the range is read.
-template <typename K, int NT, int IPT>
+// Keys [vlo, vhi) of the tile at src + lo (16-byte aligned) into registers, by NG
+// threads; rank r holds tile positions (v * NG + r) * VEC + l. Whole vectors inside the
+// range move with 128-bit loads, the edges one key at a time; nothing outside the range
+// is read.
+template <typename K, int NG, int IPT>
 __device__ __forceinline__ void tile_load(const K *src, long long lo, int vlo, int vhi,
-                                          K (&x)[IPT]) {
+                                          K (&x)[IPT], int r) {
   constexpr int VEC = Vec<K>::N, NV = IPT / VEC;
   using V = typename Vec<K>::T;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const int k0 = (v * NT + (int)threadIdx.x) * VEC;
+    const int k0 = (v * NG + r) * VEC;
     if (k0 >= vlo && k0 + VEC <= vhi) {
       const V q = __ldcg(reinterpret_cast<const V *>(src + lo + k0));
       if constexpr (VEC == 4) {
@@ -1042,7 +1043,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
         const int vlo = (int)(first > lo ? first - lo : 0);
         const int vhi = (int)(it.end - lo < TILE ? it.end - lo : TILE);
         K x[IPT];
-        tile_load<K, NT, IPT>(src, lo, vlo, vhi, x);
+        tile_load<K, NT, IPT>(src, lo, vlo, vhi, x, tid);
         unsigned cl = 0, cg = 0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -1070,7 +1071,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
         const int vlo = (int)(first > lo ? first - lo : 0);
         const int vhi = (int)(it.end - lo < TILE ? it.end - lo : TILE);
         K x[IPT];
-        tile_load<K, NT, IPT>(src, lo, vlo, vhi, x);
+        tile_load<K, NT, IPT>(src, lo, vlo, vhi, x, tid);
         unsigned lessbits = 0, gebits = 0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
@@ -3000,297 +3001,261 @@ __global__ void wave_handoff_kernel(SortParams p, int level) {
   }
 }
 
-// ----------------------------------------------------------------------------- partition rounds
-// Steps 1-4 on one array as one cooperative launch (one CTA per SM, all co-resident),
-// for the wave form. The classified keys (positions 1 .. n-1) are cut into rounds of
-// gridDim.x chunks of C keys; in round r, CTA c owns chunk r * gridDim.x + c, and each
-// warp a contiguous slice of it. Per round:
-//   stage    the chunk is copied into shared memory by bulk copies completing on an
-//            mbarrier (the next round's chunk is in flight while the current one is
-//            scattered);
-//   count    each warp counts its less keys (Step 3) with one ballot per 32 keys, and
-//            the CTA publishes its total;
-//   barrier  one bounded grid barrier;
-//   scatter  the CTA's less prefix is the less keys of earlier rounds plus the counts
-//            of the CTAs before it in this round; each warp then compacts its slice
-//            with ballots straight to global memory: less keys from the left end,
-//            >= keys from the right end, each store instruction a contiguous run.
-// After the last round CTA 0 writes the key at index #{x < key} (Step 4). Each key is
-// read once and written once, and no CTA waits on another except at the barriers.
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-template <int NW>
-struct RoundShared {
-  unsigned wl[NW], wg[NW];
-  unsigned long long red[NW], red2[NW];
-  int ok;
+// ----------------------------------------------------------------------------- split
+// A single partition (Steps 1-4 of one array) in two launches with no wait between CTAs:
+// split_count_kernel, then split_move_kernel under programmatic dependent launch. The
+// keys after the key are cut into warp tiles of 32 * IPT keys, anchored at the 16-byte
+// boundary at or below index 1 as every tile grid here is; global warp g (CTA c, warp w:
+// g = c * NW + w) owns the Q consecutive warp tiles from g * Q on. The count launch
+// stores each warp's less count (Step 3's classification) in p.wave_cnt[g]. The move
+// launch gives each warp the exclusive prefix of those counts and moves the warp's tiles
+// one by one: each is compacted in the warp's own slice of shared memory (less keys,
+// then >= keys) and written with 128-bit stores, less keys from the front of the output
+// and >= keys from the back, as the tile passes do. A warp walks its tiles from the last
+// to the first, so that the ones the count launch read last, still in L2, are read again
+// first. The last warp of the grid places the key at the total less count (Step 4).
+// Every thread keeps the next tile's loads in flight while it works on the current one.
+struct SplitGeom {
+  long long base;   // start of warp tile 0 (index 1 rounded down to 16 bytes)
+  long long tiles;  // warp tiles
+  long long per;    // warp tiles per warp (Q)
 };
+template <typename K, int WT>
+__device__ __forceinline__ SplitGeom split_geom(const K *src, long long n, long long warps) {
+  SplitGeom g;
+  g.base = tile_base(src, 0);
+  g.tiles = (n - g.base + WT - 1) / WT;
+  g.per = (g.tiles + warps - 1) / warps;
+  return g;
+}
+// Key range [vlo, vhi) of warp tile s, which starts at *lo.
+template <int WT>
+__device__ __forceinline__ void split_tile(const SplitGeom &g, long long n, long long s,
+                                           long long *lo, int *vlo, int *vhi) {
+  *lo = g.base + s * WT;
+  *vlo = (int)(1 > *lo ? 1 - *lo : 0);
+  *vhi = (int)(n - *lo < WT ? n - *lo : WT);
+}
+// Step 3 on one lane's keys of a warp tile: bit j of *less / *ge set when key j is
+// classified and goes to that side.
+template <typename K, int IPT>
+__device__ __forceinline__ void split_classify(K key, const K (&x)[IPT], int vlo, int vhi,
+                                               int lane, unsigned *less, unsigned *ge) {
+  constexpr int VEC = Vec<K>::N, NV = IPT / VEC;
+  unsigned lb = 0, gb = 0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+#pragma unroll
+    for (int l = 0; l < VEC; ++l) {
+      const int j = v * VEC + l, k = (v * 32 + lane) * VEC + l;
+      const bool valid = k >= vlo && k < vhi;
+      const bool le = goes_left(key, x[j]);
+      lb |= (unsigned)(valid && le) << j;
+      gb |= (unsigned)(valid && !le) << j;
+    }
+  }
+  *less = lb;
+  *ge = gb;
+}
 
-// Grid-wide barrier of a cooperative launch. Thread 0 of every CTA arrives on a
-// counter with a release; the last one resets it and releases the next generation,
-// which thread 0 of every CTA acquires. It orders what thread 0 wrote before the
-// barrier (the data the CTAs exchange goes through thread 0). Every wait is bounded
-// (past the limit the error is set and the call's stop flag raised) and ends early when
-// the stop flag is up. Returns false when the CTA must stop.
-template <int NW>
-__device__ __forceinline__ bool round_grid_sync(Control *ctl, unsigned *stop, unsigned *gen,
-                                                unsigned long long limit_ns, RoundShared<NW> &sh) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned target = *gen + 1u;
-    int ok = 1;
-    // release: this thread's earlier writes (the CTA's published count) become visible
-    // to every CTA that acquires the next generation
-    const unsigned arrived = atom_add_release(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1u) {
-      atomicExch(&ctl->bar_count, 0u);
-      st_release_u32(&ctl->bar_gen, target);
+// A full warp tile (every key classified: all but the array's first and last) moves
+// with unconditional 128-bit loads.
+template <typename K, int IPT>
+__device__ __forceinline__ void warp_tile_load_full(const K *t, K (&x)[IPT], int lane) {
+  constexpr int VEC = Vec<K>::N, NV = IPT / VEC;
+  using V = typename Vec<K>::T;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const V q = __ldcg(reinterpret_cast<const V *>(t + (v * 32 + lane) * VEC));
+    if constexpr (VEC == 4) {
+      x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
     } else {
-      unsigned ns = 32, polls = 0;
-      unsigned long long t0 = 0;
-      while (ld_acquire_u32(&ctl->bar_gen) != target) {
-        if ((++polls & 15u) == 0u) {
-          if (ld_relaxed(stop) != 0u) { ok = 0; break; }
-          const unsigned long long now = globaltimer();
-          if (t0 == 0) t0 = now;
-          else if (now - t0 > limit_ns) {
-            raise_error(ctl, kDevTimeout, 0xA00000000ull | blockIdx.x);
-            atomicExch(stop, 1u);
-            ok = 0;
-            break;
-          }
-        }
-        __nanosleep(ns);
-        ns = ns < 128 ? ns * 2 : 128;
-      }
+      x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
     }
-    *gen = target;
-    sh.ok = ok && ld_relaxed(stop) == 0u;
   }
+}
+template <typename K, int WT, int IPT>
+__device__ __forceinline__ void split_load(const K *src, const SplitGeom &sg, long long n,
+                                           long long s, K (&x)[IPT], int lane) {
+  long long lo;
+  int vlo, vhi;
+  split_tile<WT>(sg, n, s, &lo, &vlo, &vhi);
+  if (vlo == 0 && vhi == WT) warp_tile_load_full<K, IPT>(src + lo, x, lane);
+  else tile_load<K, 32, IPT>(src, lo, vlo, vhi, x, lane);
+}
+// Step 3's less count of one lane's keys of warp tile s.
+template <typename K, int WT, int IPT>
+__device__ __forceinline__ unsigned split_less(K key, const SplitGeom &sg, long long n,
+                                               long long s, const K (&x)[IPT], int lane) {
+  long long lo;
+  int vlo, vhi;
+  split_tile<WT>(sg, n, s, &lo, &vlo, &vhi);
+  if (vlo == 0 && vhi == WT) {
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) c += goes_left(key, x[j]) ? 1u : 0u;
+    return c;
+  }
+  unsigned lb, gb;
+  split_classify<K, IPT>(key, x, vlo, vhi, lane, &lb, &gb);
+  return (unsigned)__popc(lb);
+}
+
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) split_count_kernel(SortParams p) {
+  constexpr int NW = NT / 32, WT = 32 * IPT;
+  grid_dep_launch();  // the move launch may start; it waits for this launch's memory
+  const K *const src = static_cast<const K *>(p.keys);
+  const long long n = p.total;
+  const int lane = threadIdx.x & 31;
+  const long long g = (long long)blockIdx.x * NW + (threadIdx.x >> 5);
+  const SplitGeom sg = split_geom<K, WT>(src, n, (long long)gridDim.x * NW);
+  const K key = __ldcg(src);  // Step 1: the first element is the key
+  long long s = g * sg.per;
+  const long long s_end = s + sg.per < sg.tiles ? s + sg.per : sg.tiles;
+  unsigned cl = 0;
+  // two key sets in turn: the next tile's loads are in flight while this one is counted
+  K xa[IPT], xb[IPT];
+  if (s < s_end) split_load<K, WT, IPT>(src, sg, n, s, xa, lane);
+  while (s < s_end) {
+    if (s + 1 < s_end) split_load<K, WT, IPT>(src, sg, n, s + 1, xb, lane);
+    cl += split_less<K, WT, IPT>(key, sg, n, s, xa, lane);
+    if (++s >= s_end) break;
+    if (s + 1 < s_end) split_load<K, WT, IPT>(src, sg, n, s + 1, xa, lane);
+    cl += split_less<K, WT, IPT>(key, sg, n, s, xb, lane);
+    ++s;
+  }
+  cl = __reduce_add_sync(kFull, cl);
+  if (lane == 0) p.wave_cnt[g] = cl;
+}
+
+// One warp tile of split_move_kernel: Steps 3.1/3.2 for its keys x, given the less keys
+// of every earlier warp tile (*Erun holds them for the tiles up to and including this
+// one and is lowered by this tile's count). The keys are compacted in the warp's slice
+// `so` at offsets that share the destination's 16-byte phase, so both runs are copied
+// out with aligned 128-bit loads and stores. False (and an error) if a destination
+// falls outside the output.
+template <typename K, int WT, int IPT>
+__device__ __forceinline__ bool split_move_tile(const SortParams &p, K key, const SplitGeom &sg,
+                                                long long n, long long s, const K (&x)[IPT],
+                                                K *so, K *dst, unsigned long long *Erun,
+                                                int lane) {
+  constexpr int VEC = Vec<K>::N;
+  long long lo;
+  int vlo, vhi;
+  split_tile<WT>(sg, n, s, &lo, &vlo, &vhi);
+  const bool full = vlo == 0 && vhi == WT;
+  unsigned lb = 0, gb = 0, mine;
+  if (full && sizeof(K) == 4) {  // one compare per key: recount, and compare again below
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) c += goes_left(key, x[j]) ? 1u : 0u;
+    mine = c | ((IPT - c) << 16);
+  } else if (full) {  // 8-byte keys compare on the integer pipes: keep the result bits
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) lb |= (goes_left(key, x[j]) ? 1u : 0u) << j;
+    gb = ~lb & (IPT >= 32 ? 0xffffffffu : (1u << (IPT & 31)) - 1u);
+    mine = (unsigned)__popc(lb) | ((unsigned)(IPT - __popc(lb)) << 16);
+  } else {
+    split_classify<K, IPT>(key, x, vlo, vhi, lane, &lb, &gb);
+    mine = (unsigned)__popc(lb) | ((unsigned)__popc(gb) << 16);
+  }
+  unsigned incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned u = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += u;
+  }
+  const unsigned tot = __shfl_sync(kFull, incl, 31);
+  const unsigned L = tot & 0xffffu, G = tot >> 16;
+  const unsigned long long E = *Erun - L;  // less keys in all earlier warp tiles
+  *Erun = E;
+  const long long PV = s == 0 ? 0 : lo - 1;  // classified keys in earlier warp tiles
+  const long long lbase = (long long)E, gbase = n - (PV - (long long)E) - (long long)G;
+  if (lbase < 0 || lbase + L > n || gbase < 1 || gbase + G > n) {
+    if (lane == 0) raise_error(p.ctl, kDevInternal, 0xA00000000ull | (unsigned)s);
+    return false;
+  }
+  const unsigned ml = (unsigned)((reinterpret_cast<uintptr_t>(dst + lbase) & 15u) / sizeof(K));
+  const unsigned mg = (unsigned)((reinterpret_cast<uintptr_t>(dst + gbase) & 15u) / sizeof(K));
+  const unsigned wl0 = ml, wg0 = (ml + L + VEC - 1) / VEC * VEC + mg;
+  const unsigned ex = incl - mine;
+  if (full && sizeof(K) == 4) {
+    unsigned rl = wl0 + (ex & 0xffffu), rg = wg0 + (ex >> 16);
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const bool le = goes_left(key, x[j]);
+      so[le ? rl : rg] = x[j];
+      rl += le ? 1u : 0u;
+      rg += le ? 0u : 1u;
+    }
+  } else {
+    scatter_keys<K, IPT>(so, x, lb, gb, wl0, wg0, ex);
+  }
+  __syncwarp();
+  copy_out_v<K, 32>(so + wl0, dst + lbase, L, lane);
+  copy_out_v<K, 32>(so + wg0, dst + gbase, G, lane);
+  __syncwarp();  // the slice is refilled by the next tile
+  return true;
+}
+
+template <typename K, int NT, int IPT>
+__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) split_move_kernel(SortParams p) {
+  constexpr int VEC = Vec<K>::N, NW = NT / 32, WT = 32 * IPT;
+  static_assert(IPT % VEC == 0 && IPT <= 32 && WT < 65536, "bad warp tile");
+  // per warp: both runs at their destination phase (up to 3 * VEC keys of gaps) plus the
+  // 16 bytes copy_out_v may read past a run
+  __shared__ __align__(16) K sbuf[NW][WT + 4 * VEC];
+  __shared__ unsigned long long spart[NW];
+  const K *const src = static_cast<const K *>(p.keys);
+  K *const dst = static_cast<K *>(p.scratch);
+  const long long n = p.total;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const long long c0 = (long long)blockIdx.x * NW, g = c0 + w;
+  const SplitGeom sg = split_geom<K, WT>(src, n, (long long)gridDim.x * NW);
+  const K key = __ldcg(src);  // Step 1
+  const long long s_begin = g * sg.per < sg.tiles ? g * sg.per : sg.tiles;
+  const long long s_end = s_begin + sg.per < sg.tiles ? s_begin + sg.per : sg.tiles;
+  K xa[IPT], xb[IPT];
+  // the warp's last tile first: its loads do not depend on the count launch
+  if (s_begin < s_end) split_load<K, WT, IPT>(src, sg, n, s_end - 1, xa, lane);
+  grid_dep_wait();  // every warp's count is written and visible
+  const unsigned long long *cnt = p.wave_cnt;
+  unsigned long long acc = 0;  // less keys of the warps of earlier CTAs
+  for (long long i = tid; i < c0; i += NT) acc += __ldcg(&cnt[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  if (lane == 0) spart[w] = acc;
   __syncthreads();
-  return sh.ok != 0;
-}
-
-// Chunk of round r for CTA c: key indices [*j0, *j1) (array positions + 1), and its
-// place in a staging buffer: index *so, chosen so that the first 16-byte chunk of the
-// global copy lands 16-byte aligned; *head keys precede that chunk.
-template <typename K>
-__device__ __forceinline__ void round_chunk(const K *in, long long m, int r, int c, int G, int C,
-                                            long long *j0, long long *j1, int *head, int *so) {
-  constexpr int V16 = 16 / (int)sizeof(K);
-  const long long a = ((long long)r * G + c) * C;
-  *j0 = a < m ? a : m;
-  *j1 = a + C < m ? a + C : m;
-  const K *gp = in + 1 + *j0;
-  const int h = (int)(((16u - (unsigned)(reinterpret_cast<uintptr_t>(gp) & 15u)) & 15u) / sizeof(K));
-  *head = h;
-  *so = (V16 - h % V16) % V16;
-}
-
-// Thread 0: the 16-byte-aligned body of chunk [j0, j1) goes to its staging buffer by
-// bulk copies (pieces of at most 64 KB) completing on `bar`; the head and tail keys
-// around it are read with plain loads by round_edges when the chunk is used.
-template <typename K>
-__device__ __forceinline__ void round_stage_bulk(const K *in, long long j0, long long j1,
-                                                 int head, int so, K *buf,
-                                                 unsigned long long *bar) {
-  constexpr int V16 = 16 / (int)sizeof(K);
-  const int n = (int)(j1 - j0);
-  const int h = head < n ? head : n;
-  const unsigned bytes = (unsigned)((n - h) / V16) * 16u;
-  const char *gp = reinterpret_cast<const char *>(in + 1 + j0 + h);
-  char *sp = reinterpret_cast<char *>(buf + so + h);
-  fence_proxy_async();  // the buffer's earlier reads come before the copy's writes
-  mbar_expect_tx(bar, bytes);
-  for (unsigned off = 0; off < bytes; off += 65536u) {
-    const unsigned len = bytes - off < 65536u ? bytes - off : 65536u;
-    bulk_g2s(sp + off, gp + off, len, bar);
+  unsigned long long E0 = 0;
+#pragma unroll
+  for (int i = 0; i < NW; ++i) E0 += spart[i];
+  for (int i = 0; i < w; ++i) E0 += __ldcg(&cnt[c0 + i]);  // earlier warps of this CTA
+  const unsigned long long mine_cnt = __ldcg(&cnt[g]);
+  if (blockIdx.x == gridDim.x - 1 && w == NW - 1 && lane == 0) {
+    const unsigned long long c = E0 + mine_cnt;  // #{x < key} over the whole array
+    if (c >= (unsigned long long)n) {
+      raise_error(p.ctl, kDevInternal, 0xA00000000ull);
+    } else {
+      dst[c] = key;  // Step 4
+      if (p.key_index) *p.key_index = (long long)c;
+    }
   }
-}
-
-// Whole CTA: the keys of chunk [j0, j1) outside its bulk-copied body.
-template <typename K, int NT>
-__device__ __forceinline__ void round_edges(const K *in, long long j0, long long j1, int head,
-                                            int so, K *buf) {
-  constexpr int V16 = 16 / (int)sizeof(K);
-  const int n = (int)(j1 - j0);
-  const int h = head < n ? head : n;
-  const int body_end = h + (n - h) / V16 * V16;
-  const K *gp = in + 1 + j0;
-  K *sp = buf + so;
-  for (int i = threadIdx.x; i < h; i += NT) sp[i] = __ldcg(gp + i);
-  for (int i = body_end + threadIdx.x; i < n; i += NT) sp[i] = __ldcg(gp + i);
-}
-
-template <typename K, int NT>
-__global__ void __launch_bounds__(NT, 1) part_round_kernel(SortParams p, int C) {
-  constexpr int NW = NT / 32, V16 = 16 / (int)sizeof(K);
-  extern __shared__ __align__(16) unsigned char round_smem[];
-  const int CS = C + V16;  // one staging buffer, a multiple of V16 keys
-  K *const stage0 = reinterpret_cast<K *>(round_smem);
-  __shared__ RoundShared<NW> sh;
-  __shared__ unsigned wcnt[NW];  // less keys of each warp's slice in this round
-  __shared__ __align__(8) unsigned long long bar[2];  // bulk copies into buffer 0 / 1
-  Control *ctl = p.ctl;
-  const K *in = static_cast<const K *>(p.keys);
-  K *out = static_cast<K *>(p.scratch);
-  const long long n = p.total, m = n - 1;
-  const int G = (int)gridDim.x, c = (int)blockIdx.x, tid = threadIdx.x;
-  const int lane = tid & 31, w = tid >> 5;
-  const unsigned lt = lanemask_lt();
-  const K key = __ldcg(in);  // Step 1: the first element is the key
-  const int R = (int)((m + (long long)G * C - 1) / ((long long)G * C));
-  unsigned gen = 0;
-  if (tid == 0) gen = ld_acquire_u32(&ctl->bar_gen);  // the same in every CTA until all arrive
-  long long j0 = 0, j1 = 0;
-  int head = 0, so = 0;
-  round_chunk<K>(in, m, 0, c, G, C, &j0, &j1, &head, &so);
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    fence_mbar_init();
-    round_stage_bulk<K>(in, j0, j1, head, so, stage0, &bar[0]);
-  }
-  __syncthreads();  // no thread touches the barriers before they are initialised
-  unsigned long long running = 0;  // less keys of the earlier rounds
-  int staged = 1, consumed = 0;      // rounds whose chunk was requested / has landed
+  unsigned long long Erun = E0 + mine_cnt;  // less keys up to the next tile back
+  K *const so = sbuf[w];
   bool ok = true;
-  for (int r = 0; r < R && ok; ++r) {
-    K *buf = stage0 + (r & 1) * CS;
-    if (r + 1 < R) {  // the next chunk streams in during this whole round
-      if (tid == 0) {
-        long long k0 = 0, k1 = 0;
-        int h2 = 0, so2 = 0;
-        round_chunk<K>(in, m, r + 1, c, G, C, &k0, &k1, &h2, &so2);
-        round_stage_bulk<K>(in, k0, k1, h2, so2, stage0 + ((r + 1) & 1) * CS, &bar[(r + 1) & 1]);
-      }
-      staged = r + 2;
-    }
-    round_chunk<K>(in, m, r, c, G, C, &j0, &j1, &head, &so);
-    const int nloc = (int)(j1 - j0);
-    // warp w owns the slice [w0, w1) of the chunk, whole 32-key groups but the last
-    const int S = (nloc + NW * 32 - 1) / (NW * 32) * 32;
-    const int w0 = min(w * S, nloc), w1 = min(w0 + S, nloc);
-    round_edges<K, NT>(in, j0, j1, head, so, buf);
-    if (!mbar_wait(&bar[r & 1], (unsigned)(r >> 1) & 1u, p.spin_limit_ns)) {
-      if (tid == 0) {
-        raise_error(ctl, kDevTimeout, 0xC00000000ull | (unsigned)c);
-        atomicExch(&ctl->part_abort, 1u);
-      }
-      ok = false;
-    }
-    if (__syncthreads_or(!ok)) ok = false;
-    if (!ok) break;
-    consumed = r + 1;
-    const K *sp = buf + so;
-    unsigned cnt = 0;
-    for (int g = w0; g < w1; g += 128) {  // Step 3, one ballot per 32 keys, 4 in flight
-      bool le[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = g + u * 32 + lane;
-        le[u] = i < w1 && goes_left(key, sp[i < w1 ? i : w0]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) cnt += __popc(__ballot_sync(kFull, le[u]));
-    }
-    if (lane == 0) wcnt[w] = cnt;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long t = 0;
-#pragma unroll
-      for (int i = 0; i < NW; ++i) t += wcnt[i];
-      p.wave_cnt[(size_t)(r & 1) * G + c] = t;
-    }
-    if (!(ok = round_grid_sync<NW>(ctl, &ctl->part_abort, &gen, p.spin_limit_ns, sh))) break;
-    // less keys before this chunk: earlier rounds, then the CTAs before it in this round
-    unsigned long long before_c = 0, total = 0;
-    for (int q = tid; q < G; q += NT) {
-      const unsigned long long v = __ldcg(&p.wave_cnt[(size_t)(r & 1) * G + q]);
-      total += v;
-      if (q < c) before_c += v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      before_c += __shfl_xor_sync(kFull, before_c, o);
-      total += __shfl_xor_sync(kFull, total, o);
-    }
-    if (lane == 0) {
-      sh.red[w] = before_c;
-      sh.red2[w] = total;
-    }
-    __syncthreads();
-    before_c = total = 0;
-    unsigned before_w = 0;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      before_c += sh.red[i];
-      total += sh.red2[i];
-      if (i < w) before_w += wcnt[i];
-    }
-    // this warp's less keys go to out[lb ...]; its >= keys fill [gb, gb + its >= count)
-    // from the left, after the >= keys of every later slice: counted from the right end
-    long long lb = (long long)(running + before_c) + before_w;
-    const long long ge_before = (j0 + w0) - lb;  // >= keys before this slice
-    long long gb = n - ge_before - (long long)((w1 - w0) - (int)wcnt[w]);
-    if (!(lb >= 0 && lb + wcnt[w] <= n && gb >= 0 && gb + ((w1 - w0) - (int)wcnt[w]) <= n)) {
-      if (lane == 0) {
-        raise_error(ctl, kDevInternal, 0xB00000000ull | (unsigned)c);
-        atomicExch(&ctl->part_abort, 1u);
-      }
-      ok = false;
-    }
-    if (__syncthreads_or(!ok)) ok = false;
-    if (!ok) break;
-    for (int g = w0; g < w1; g += 128) {  // four groups of 32 keys in flight
-      K x[4];
-      unsigned bl[4], bg[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int i = g + u * 32 + lane;
-        const bool valid = i < w1;
-        x[u] = sp[valid ? i : w0];
-        const bool le = valid && goes_left(key, x[u]);
-        bl[u] = __ballot_sync(kFull, le);
-        bg[u] = __ballot_sync(kFull, valid && !le);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if ((bl[u] >> lane) & 1u) out[lb + __popc(bl[u] & lt)] = x[u];
-        else if ((bg[u] >> lane) & 1u) out[gb + __popc(bg[u] & lt)] = x[u];
-        lb += __popc(bl[u]);
-        gb += __popc(bg[u]);
-      }
-    }
-    running += total;
-    __syncthreads();  // wcnt and the buffer are reused two rounds on
+  // from the last tile to the first, two key sets in turn (the next loads in flight)
+  long long s = s_end - 1;
+  while (s >= s_begin) {
+    if (s > s_begin) split_load<K, WT, IPT>(src, sg, n, s - 1, xb, lane);
+    if (!(ok = split_move_tile<K, WT, IPT>(p, key, sg, n, s, xa, so, dst, &Erun, lane))) break;
+    if (--s < s_begin) break;
+    if (s > s_begin) split_load<K, WT, IPT>(src, sg, n, s - 1, xa, lane);
+    if (!(ok = split_move_tile<K, WT, IPT>(p, key, sg, n, s, xb, so, dst, &Erun, lane))) break;
+    --s;
   }
-  if (tid == 0) {
-    // a chunk requested but not used (a stopped call) may still be landing: wait for it,
-    // bounded, before the CTA's shared memory is released
-    for (int q = consumed; q < staged; ++q)
-      (void)mbar_wait(&bar[q & 1], (unsigned)(q >> 1) & 1u, p.spin_limit_ns);
-  }
-  if (ok && c == 0 && tid == 0) {
-    out[running] = key;  // Step 4: the key's final index is #{x < key}
-    if (p.key_index) *p.key_index = (long long)running;
-  }
-  // the last CTA out leaves the barrier and stop flag clear for the next call
-  if (tid == 0) {
-    __threadfence();
-    if (atomicAdd(&ctl->part_done, 1u) == (unsigned)G - 1u) {
-      ctl->bar_count = 0u;
-      ctl->part_abort = 0u;
-      __threadfence();
-      ctl->part_done = 0u;
-    }
-  }
+  if (ok && Erun != E0 && lane == 0)  // the counts of both launches disagree
+    raise_error(p.ctl, kDevInternal, 0xA00000000ull | 0xFFFFFFFFull);
 }
 
 // Phase 2: every small sub-array, claimed from the complete list, is loaded into shared

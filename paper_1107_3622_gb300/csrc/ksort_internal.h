@@ -57,8 +57,6 @@ struct alignas(128) Control {
   // level-synchronous passes: per level parity, items << kWaveKeyBits | classified keys
   unsigned long long wave_ctr[2];
   unsigned long long wave_fin;  // keys of an even level waiting for their final index
-  unsigned bar_count;           // grid barrier of part_round_kernel: CTAs arrived
-  unsigned bar_gen;             // and its generation (only ever incremented)
 };
 
 // Level-synchronous partition passes (the wave form): the sub-arrays above the cutoff
@@ -167,9 +165,9 @@ struct Launcher {
                                 cudaStream_t s);
   static cudaError_t wave_handoff(const SortParams &p, int shape, int level, bool pdl,
                                   cudaStream_t s);
-  // single partitions of the wave form: part_round_kernel, one cooperative launch of one
-  // CTA per SM over rounds of staged chunks (n >= 2)
-  static cudaError_t partition_rounds(const SortParams &p, int shape, int sms, cudaStream_t s);
+  // single partitions of the wave form: split_count_kernel, then split_move_kernel under
+  // programmatic dependent launch (n >= 2; the per-warp counts go to p.wave_cnt)
+  static cudaError_t partition_split(const SortParams &p, int shape, int sms, cudaStream_t s);
 };
 
 }  // namespace ksort

@@ -234,51 +234,40 @@ cudaError_t Launcher<K>::wave_handoff(const SortParams &p, int shape, int level,
   });
 }
 
-// part_round_kernel with the CTA size of shape `shape`: one CTA per SM with two staging
-// buffers of as many keys as the device's shared memory allows (fewer when the array
-// needs fewer), launched cooperatively so that all CTAs are co-resident.
+// split_count_kernel then split_move_kernel (the latter under programmatic dependent
+// launch) with the CTA shape of `shape`: as many CTAs as are co-resident, no more than
+// the warp tiles need, and no more warps than p.wave_cnt holds counts.
 template <typename K>
-cudaError_t Launcher<K>::partition_rounds(const SortParams &p, int shape, int sms,
-                                          cudaStream_t st) {
+cudaError_t Launcher<K>::partition_split(const SortParams &p, int shape, int sms,
+                                         cudaStream_t st) {
   return with_shape<K>(shape % kTileShapes, [&](auto s) {
     using S = decltype(s);
-    constexpr int V16 = 16 / (int)sizeof(K);
-    auto fn = dev::part_round_kernel<K, S::NT>;
-    int dev_id = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev_id);
+    constexpr int NW = S::NT / 32, WT = 32 * S::IPT;
+    auto count = dev::split_count_kernel<K, S::NT, S::IPT>;
+    auto move = dev::split_move_kernel<K, S::NT, S::IPT>;
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, count, S::NT, 0);
     if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, move, S::NT, 0);
     if (e != cudaSuccess) return e;
-    cudaFuncAttributes fa{};
-    e = cudaFuncGetAttributes(&fa, fn);
+    const long long per_sm = std::max(1, std::min(a, b));
+    const long long wtiles = (p.total + WT) / WT;  // at least the warp tiles there are
+    long long grid = std::min<long long>((long long)sms * per_sm, (wtiles + NW - 1) / NW);
+    grid = std::max<long long>(1, std::min<long long>(grid, 2 * kWaveMaxGrid / NW));
+    count<<<(int)grid, S::NT, 0, st>>>(p);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long room = (long long)optin - (long long)fa.sharedSizeBytes - 1024;
-    const long long cap = room / 2 / (long long)sizeof(K) / V16 * V16 - V16;  // keys per buffer
-    if (cap < V16) return cudaErrorInvalidConfiguration;
-    const size_t smem_max = (size_t)(2 * (cap + V16)) * sizeof(K);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, S::NT, smem_max);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int g = (int)std::min<long long>((long long)sms * per_sm, kWaveMaxGrid);
-    // equal chunks for small arrays (one round), else full buffers
-    const long long m = p.total - 1;
-    const long long share = ((m + g - 1) / g + V16 - 1) / V16 * V16;
-    const long long C = std::max<long long>(V16, std::min(cap, share));
-    const size_t smem = (size_t)(2 * (C + V16)) * sizeof(K);
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)g);
+    cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)S::NT);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, fn, p, (int)C);
+    return cudaLaunchKernelEx(&cfg, move, p);
   });
 }
 

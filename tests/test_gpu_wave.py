@@ -4,9 +4,9 @@ the work queue finishes what remains. Every result must stay byte-identical to t
 oracle whatever the number of wave levels (the hand-off to the queue can happen at any
 depth), at both ends of the cutoff range, on degenerate and duplicate-heavy inputs, on
 batches (many roots on one level list) and under CUDA-graph capture. Single partitions:
-one cooperative launch streaming staged chunks in rounds, checked against the oracle's
-key index and side multisets for every key type, one to several rounds, unaligned
-starts, in place, and interleaved with part_kernel calls."""
+a counting launch and a moving launch over runs of warp tiles per warp, checked against
+the oracle's key index and side multisets for every key type, from one warp tile to
+many per warp, unaligned starts, in place, and interleaved with part_kernel calls."""
 import numpy as np
 import pytest
 
@@ -157,6 +157,7 @@ def test_wave_stats_and_bad_offsets(ks, restore):
     assert st["small_items"] <= st["items_pushed"] <= st["large_items"] + st["small_items"]
     # kernels per call as the library counts them: seed, two per wave level, hand-off,
     # queue, finisher; the queue form: seed, tile passes, finisher; a partition: one
+    # (part_kernel) or two (the wave form's count and move)
     ks.ksort_set_tuning(ks.F32, wave_levels=5)
     ks.sort_(t)
     assert ks.ksort_get_stats()["launches"] == 2 * 5 + 4
@@ -166,6 +167,8 @@ def test_wave_stats_and_bad_offsets(ks, restore):
     ks.partition_(t)
     assert ks.ksort_get_stats()["launches"] == 1
     ks.ksort_set_tuning(ks.F32, tile_shape=10)
+    ks.partition_(t)
+    assert ks.ksort_get_stats()["launches"] == 2
     flat = _dev(gen.uniform_f32(1, 10_000))
     bad = _dev(np.array([0, 6000, 4000, 10_000], np.int64))
     ks.sort_batched_(flat, bad)
@@ -212,9 +215,9 @@ def _check_partition(ref, ks, code, a, offset=0, in_place=False):
 
 @pytest.mark.parametrize("shape", WAVE)
 @pytest.mark.parametrize("dtype", list(DTYPES))
-def test_wave_partition_rounds(ref, ks, restore, dtype, shape):
-    """Single partitions of the wave form (one cooperative launch streaming staged
-    chunks in rounds): one chunk per CTA, partial rounds, and several full rounds."""
+def test_wave_partition_split(ref, ks, restore, dtype, shape):
+    """Single partitions of the wave form (count, then move): a single warp tile, fewer
+    warp tiles than warps, and many warp tiles per warp."""
     code = DTYPES[dtype]
     ks.ksort_set_tuning(code, tile_shape=shape)
     for n in (2, 3, 31, 4097, 100_003, 1_000_001, 7_000_000):
@@ -227,9 +230,9 @@ def test_wave_partition_rounds(ref, ks, restore, dtype, shape):
 
 
 def test_wave_partition_alternates_with_part_kernel(ref, ks, restore):
-    """Calls of the cooperative partition and of part_kernel interleave on one stream
-    (both leave the shared barrier and stop flags clear), including key classes the
-    IEEE compare treats specially."""
+    """Calls of the split partition and of part_kernel interleave on one stream (the
+    counts of one and the descriptors of the other share a workspace), including key
+    classes the IEEE compare treats specially."""
     for rep in range(6):
         for shape in (10, 1, 12, 3):
             ks.ksort_set_tuning(ks.F32, tile_shape=shape)
