@@ -3,7 +3,7 @@
 tile and then moves them with the prefixes it has summed itself, without look-back.
 Every result must stay byte-identical to the oracle for each limit, key type and input
 class (random, duplicate-heavy, presorted), in single sorts, batches and the wave form's
-queue. (Single partitions run part_kernel or the round kernel, never the queue.)"""
+queue. (Single partitions run part_kernel or the split partition, never the queue.)"""
 import numpy as np
 import pytest
 

@@ -119,5 +119,6 @@ def test_autotuner_partition_kind(ks, restore, tmp_path, monkeypatch):
     assert e["workload"] == "partition:f32:2^19"
     # only the form of the tile passes is searched for a single partition
     assert {c["cutoff"] for c in e["candidates"]} == {e["tuning"]["cutoff"]}
-    assert len(e["candidates"]) == 3  # the three CTA shapes of part_kernel
+    # the three CTA shapes of part_kernel and of the split partition (the wave form)
+    assert sorted(c["tile_shape"] for c in e["candidates"]) == [1, 2, 3, 10, 11, 12]
     assert ks.ksort_get_tuning(ks.F32)["tile_shape"] == e["tuning"]["tile_shape"]

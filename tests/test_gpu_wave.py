@@ -247,3 +247,35 @@ def test_wave_partition_alternates_with_part_kernel(ref, ks, restore):
     for key in (np.nan, -0.0, np.inf, 1.0):
         a[0] = key
         _check_partition(ref, ks, ks.F64, a)
+
+
+def test_wave_partition_in_graph(ref, ks, restore):
+    """The split partition captured in a CUDA graph (the move launch depends on the count
+    launch programmatically) and replayed, with the output cleared between replays."""
+    import torch
+    ks.ksort_set_tuning(ks.F32, tile_shape=10)
+    n = 1_000_003
+    a = gen.make("uniform", "f32", n, gen.seed_for(9, 110, 0))
+    src = _dev(a)
+    dst = torch.empty_like(src)
+    idx = torch.empty(1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ks.ksort_reserve_workspace(ks.F32, n, 1, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ks.ksort_partition_out(ks.F32, src, dst, n, idx, stream=s)
+    b = a.copy()
+    ri, *_ = ref.partition(b)
+    for _ in range(3):
+        dst.zero_()
+        idx.fill_(-1)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(idx.item()) == ri
+        got = dst.cpu().numpy()
+        assert got[ri:ri + 1].tobytes() == a[:1].tobytes()
+        assert _bits(got[:ri]) == _bits(b[:ri]) and _bits(got[ri + 1:]) == _bits(b[ri + 1:])
+    assert ks.ksort_get_device_error(s) == 0
