@@ -143,3 +143,27 @@ def test_autotune_workload_keys():
     k = autotune.workload_key("batched", 2, lengths=np.array([100, 1000, 500_000]))
     assert k == "batched:u32:3x[100,500000]:2^19"
     assert len(autotune.library_hash()) == 16
+
+
+def _header_structs():
+    """{typedef name: [(field, C type), ...]} of every plain struct in include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+            out[name] = re.findall(r"(\w+)\s+(\w+)\s*;", body)
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of the header's structs have the same fields, in the same order
+    and of the same C types, so every call that passes one reads what the library wrote."""
+    import paper_1107_3622_gb300 as ks
+    ctype = {"int32_t": ctypes.c_int32, "uint64_t": ctypes.c_uint64, "int64_t": ctypes.c_int64}
+    structs = _header_structs()
+    for name, mirror in (("ksort_tuning_t", ks.Tuning), ("ksort_stats_t", ks.Stats)):
+        fields = structs[name]
+        assert [f for _, f in fields] == [n for n, _ in mirror._fields_], name
+        assert [ctype[t] for t, _ in fields] == [c for _, c in mirror._fields_], name
+        assert ctypes.sizeof(mirror) == sum(ctypes.sizeof(ctype[t]) for t, _ in fields)
+
