@@ -460,31 +460,52 @@ def run_ours(args, dist: Dist):
 
 
 def run_e2e(ks, host, args, stream):
+    """Whole-job throughput through the public API from pinned host memory: every step
+    copies its input to the device, sorts it and copies the result back. Two streams
+    double-buffer the steps, so one step's copies run beside the previous step's sort;
+    the sorts themselves run one at a time (each waits for the previous one's event)."""
     import torch
     n = len(host)
-    pinned = torch.from_numpy(host).pin_memory()
-    back = torch.empty_like(pinned).pin_memory()
-    dkeys = torch.empty(n, dtype=torch.float32, device="cuda")
-    steps = max(5, min(args.steps, 30))
-    for _ in range(2):
-        dkeys.copy_(pinned, non_blocking=True)
-        ks.sort_(dkeys)
-        back.copy_(dkeys, non_blocking=True)
+    pinned = [torch.from_numpy(host).pin_memory() for _ in range(2)]
+    back = [torch.empty_like(pinned[0]).pin_memory() for _ in range(2)]
+    dkeys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(2)]
+    lanes = [torch.cuda.Stream() for _ in range(2)]
+    steps = max(6, min(args.steps, 30))
+
+    def run(k):
+        prev = None
+        for i in range(k):
+            j = i % 2
+            s = lanes[j]
+            with torch.cuda.stream(s):
+                dkeys[j].copy_(pinned[j], non_blocking=True)  # after this lane's last D2H
+                if prev is not None:
+                    s.wait_event(prev)  # one sort at a time
+                ks.sort_(dkeys[j], stream=s)
+                prev = torch.cuda.Event()
+                prev.record(s)
+                back[j].copy_(dkeys[j], non_blocking=True)
+
+    run(4)  # warm-up: workspaces of both streams
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(steps):
-        dkeys.copy_(pinned, non_blocking=True)
-        ks.sort_(dkeys)
-        back.copy_(dkeys, non_blocking=True)
+    for s in lanes:
+        s.wait_event(t0)
+    run(steps)
+    for s in lanes:
+        stream.wait_stream(s)
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / steps
-    assert bool((back[1:] >= back[:-1]).all())
+    for b in back:
+        assert bool((b[1:] >= b[:-1]).all())
     return {"value": round(n / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 4),
             "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
-            "path": "pinned host -> cudaMemcpyAsync -> ksort_sort -> cudaMemcpyAsync -> host"}
+            "path": "pinned host -> cudaMemcpyAsync -> ksort_sort -> cudaMemcpyAsync -> host, "
+                    "two streams double-buffered (copies beside the other step's sort; "
+                    "one sort at a time)"}
 
 
 def run_partition_pass(ks, n, peak, peak_src, args):
