@@ -182,10 +182,10 @@ KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *o
  *   tile_shape:    form of the partition passes, 1 .. 12 (1 = default); see
  *                  ksort_tile_shape(). Changing it may grow a stream's workspace on
  *                  the next call, so reserve again before capturing a graph.
- *   wave_levels:   forms 10 .. 12 only: recursion levels run as level-synchronous
+ *   wave_levels:   tile shapes 10 .. 12 only: recursion levels run as level-synchronous
  *                  passes before the work queue takes over (1 .. 64); -1 = automatic
  *                  (about log2 of the mean array length over the cutoff, plus 2).
- *   medium_tiles:  forms 1 .. 3 and 10 .. 12 (the register form's work queue): a
+ *   medium_tiles:  tile shapes 1 .. 3 and 10 .. 12 (the register form's work queue): a
  *                  sub-array of 2 .. medium_tiles tile passes is taken by one CTA, which
  *                  counts every tile first and then moves them with the prefixes it
  *                  knows (no look-back); 1 .. 16, -1 = off (the default).
