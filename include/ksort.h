@@ -172,6 +172,22 @@ typedef struct {
 } ksort_stats_t;
 KSORT_API ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out);
 
+/* Phase timing, for the roofline report (off by default). While enabled (enable != 0),
+ * every ksort_sort, ksort_sort_batched, ksort_partition and ksort_partition_out call made
+ * outside CUDA-graph capture records CUDA events on its stream at the boundaries of its
+ * phases. A sort has three phases: the seed kernel; the partition passes (the tile
+ * kernel, and the wave form's levels and hand-off); the shared-memory finisher. A
+ * partition has one: its launch (two launches in the wave form). The events cost a few
+ * microseconds of device time per call. */
+KSORT_API ksort_status_t ksort_set_phase_timing(int32_t enable);
+/* Synchronises `stream`, then writes the phase durations in milliseconds of up to
+ * `max_calls` of the most recent timed calls on it (the last 64 are kept), oldest first,
+ * three floats per call: out_ms[3 * c + i] is phase i of call c, and -1 for a phase the
+ * call does not have (a partition has only phase 0). out_ms holds 3 * max_calls floats;
+ * *calls receives the number of calls written (0 when none on `stream` was timed). */
+KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t max_calls,
+                                               float *out_ms, int32_t *calls);
+
 /* Tuning for one dtype (process-wide; the autotuner sets it). Zero fields keep their
  * current value.
  *   cutoff:        sub-arrays with at most this many keys are finished in shared

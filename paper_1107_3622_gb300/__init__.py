@@ -21,7 +21,9 @@ __all__ = [
     "ksort_partition", "ksort_partition_out", "ksort_partition_out_noalloc",
     "ksort_partition_exact", "partition_exact", "ksort_sort", "ksort_sort_batched",
     "ksort_reserve_workspace", "ksort_release_workspace", "ksort_get_device_error",
-    "ksort_get_stats", "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
+    "ksort_get_stats", "ksort_set_phase_timing", "ksort_get_phase_times",
+    "ksort_get_phase_history",
+    "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
     "ksort_tile_keys", "ksort_tile_shape", "ksort_status_string", "ksort_last_cuda_error",
     "ksort_selftest_wait_timeout", "ksort_debug_trace",
     "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
@@ -96,6 +98,9 @@ def load():
             "ksort_release_workspace": (i32, [vp]),
             "ksort_get_device_error": (i32, [vp]),
             "ksort_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+            "ksort_set_phase_timing": (i32, [i32]),
+            "ksort_get_phase_times": (i32, [vp, i32, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_int32)]),
             "ksort_set_tuning": (i32, [i32, ctypes.POINTER(Tuning)]),
             "ksort_get_tuning": (i32, [i32, ctypes.POINTER(Tuning)]),
             "ksort_max_cutoff": (i32, [i32]),
@@ -214,6 +219,26 @@ def ksort_get_stats(stream=None) -> dict:
     s = Stats()
     _check(load().ksort_get_stats(_stream(stream), ctypes.byref(s)), "ksort_get_stats")
     return s.as_dict()
+
+
+def ksort_set_phase_timing(enable: bool):
+    _check(load().ksort_set_phase_timing(1 if enable else 0), "ksort_set_phase_timing")
+
+
+def ksort_get_phase_history(stream=None, max_calls: int = 64) -> list:
+    """Phase durations (ms) of up to max_calls of the latest timed calls on the stream,
+    oldest first: [seed, partition passes, finisher] per sort, [partition] per partition."""
+    out = (ctypes.c_float * (3 * max(1, max_calls)))()
+    calls = ctypes.c_int32(0)
+    _check(load().ksort_get_phase_times(_stream(stream), max_calls, out, ctypes.byref(calls)),
+           "ksort_get_phase_times")
+    return [[float(v) for v in out[3 * c:3 * c + 3] if v >= 0.0] for c in range(calls.value)]
+
+
+def ksort_get_phase_times(stream=None) -> list:
+    """Phase durations (ms) of the last timed call on the stream ([] if none)."""
+    h = ksort_get_phase_history(stream, 1)
+    return h[0] if h else []
 
 
 def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0,

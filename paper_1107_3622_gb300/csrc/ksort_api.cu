@@ -106,6 +106,49 @@ struct Workspace {
 
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
+// ------------------------------------------------------------------ phase timing
+// While enabled, a sort or partition call outside graph capture records CUDA events on
+// its stream at the boundaries of its phases (4 for a sort: before the seed, after it,
+// after the partition passes, after the finisher; 2 for a partition). The events of the
+// last kPhaseRing timed calls per stream are kept, so calls can be enqueued back to back
+// and read afterwards.
+bool g_time_phases = false;
+constexpr int kPhaseMarks = 4, kPhasesOut = kPhaseMarks - 1, kPhaseRing = 64;
+struct PhaseEvents {
+  cudaEvent_t ev[kPhaseRing][kPhaseMarks] = {};
+  int marks[kPhaseRing] = {};  // events recorded by the call in each slot
+  long long calls = 0;         // timed calls so far; call c used slot c % kPhaseRing
+};
+std::map<std::pair<int, cudaStream_t>, PhaseEvents> g_phase;
+
+struct PhaseMarks {
+  PhaseEvents *pe = nullptr;  // null: this call is not timed
+  int slot = 0;
+  cudaStream_t s = nullptr;
+  cudaError_t mark() {
+    if (!pe || pe->marks[slot] >= kPhaseMarks) return cudaSuccess;
+    return cudaEventRecord(pe->ev[slot][pe->marks[slot]++], s);
+  }
+};
+
+ksort_status_t phase_begin(int dev, cudaStream_t s, PhaseMarks *m) {
+  m->pe = nullptr;
+  m->s = s;
+  if (!g_time_phases) return KSORT_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  KS_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return KSORT_OK;
+  PhaseEvents &pe = g_phase[{dev, s}];
+  const int slot = (int)(pe.calls % kPhaseRing);
+  for (cudaEvent_t &e : pe.ev[slot])
+    if (!e) KS_CUDA(cudaEventCreate(&e));
+  pe.marks[slot] = 0;
+  ++pe.calls;
+  m->pe = &pe;
+  m->slot = slot;
+  return KSORT_OK;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Bytes past the scratch keys that bulk copies of whole 16-byte chunks may read.
@@ -387,6 +430,9 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   p.key_index = reinterpret_cast<long long *>(key_index);
   p.readable[0] = n;
   p.readable[1] = 0;  // buffer 1 is only written
+  PhaseMarks pm;
+  if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
+  KS_CUDA(pm.mark());
   if (ops(dt).info(tu.variant).form == kWaveForm) {
     KS_CUDA(ops(dt).partition_split(p, shape, sms, s));
     ws->launches = 2;
@@ -394,6 +440,7 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
     KS_CUDA(ops(dt).partition(p, shape, grid, s));
     ws->launches = 1;
   }
+  KS_CUDA(pm.mark());
   if (in_place) KS_CUDA(cudaMemcpyAsync(const_cast<void *>(in), dst, n * kb, cudaMemcpyDeviceToDevice, s));
   return KSORT_OK;
 }
@@ -479,18 +526,30 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     const int levels = tu.wave_levels > 0 ? tu.wave_levels
                                           : auto_wave_levels(total, p.num_roots, tu.cutoff);
     p.wave = 1;
+    PhaseMarks pm;
+    if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
+    KS_CUDA(pm.mark());
     KS_CUDA(ops(dt).seed(p, tu.variant, s));
+    KS_CUDA(pm.mark());
     for (int l = 0; l < levels; ++l) KS_CUDA(ops(dt).wave_level(p, shape, l, (int)grid, true, s));
     KS_CUDA(ops(dt).wave_handoff(p, shape, levels, true, s));
     KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
+    KS_CUDA(pm.mark());
     KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+    KS_CUDA(pm.mark());
     ws->launches = 2ull * (unsigned long long)levels + 4ull;
     return KSORT_OK;
   }
+  PhaseMarks pm;
+  if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
+  KS_CUDA(pm.mark());
   KS_CUDA(ops(dt).seed(p, tu.variant, s));
+  KS_CUDA(pm.mark());
   const bool tiles = offsets || total > tu.cutoff;
   if (tiles) KS_CUDA(ops(dt).tiles(p, tu.variant, g.tiles, s));
+  KS_CUDA(pm.mark());
   KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+  KS_CUDA(pm.mark());
   ws->launches = tiles ? 3ull : 2ull;
   return KSORT_OK;
 }
@@ -683,6 +742,14 @@ ksort_status_t ksort_release_workspace(ksort_stream_t stream) {
   if (st != KSORT_OK) return st;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_ws.find({dev, (cudaStream_t)stream});
+  auto ph = g_phase.find({dev, (cudaStream_t)stream});
+  if (ph != g_phase.end()) {
+    KS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (auto &slot : ph->second.ev)
+      for (cudaEvent_t e : slot)
+        if (e) KS_CUDA(cudaEventDestroy(e));
+    g_phase.erase(ph);
+  }
   if (it == g_ws.end()) return KSORT_OK;
   KS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   if (it->second.base) KS_CUDA(cudaFree(it->second.base));
@@ -730,6 +797,39 @@ ksort_status_t ksort_get_stats(ksort_stream_t stream, ksort_stats_t *out) {
   out->lookback_steps = c.lookback_steps;
   out->items_pushed = c.pushed;  // pool slots: large and small items
   out->launches = it->second.launches;
+  return KSORT_OK;
+}
+
+ksort_status_t ksort_set_phase_timing(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_time_phases = enable != 0;
+  return KSORT_OK;
+}
+
+ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t max_calls, float *out_ms,
+                                     int32_t *calls) {
+  if (!calls || max_calls < 0 || (max_calls > 0 && !out_ms)) return KSORT_ERR_INVALID_ARG;
+  *calls = 0;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  KS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_phase.find({dev, (cudaStream_t)stream});
+  if (it == g_phase.end()) return KSORT_OK;
+  const PhaseEvents &pe = it->second;
+  const long long kept = std::min<long long>(pe.calls, kPhaseRing);
+  const long long n = std::min<long long>(kept, max_calls);
+  for (long long c = 0; c < n; ++c) {  // oldest of the last n first
+    const int slot = (int)((pe.calls - n + c) % kPhaseRing);
+    float *o = out_ms + c * kPhasesOut;
+    for (int i = 0; i < kPhasesOut; ++i) {
+      float ms = -1.f;
+      if (i + 1 < pe.marks[slot]) KS_CUDA(cudaEventElapsedTime(&ms, pe.ev[slot][i], pe.ev[slot][i + 1]));
+      o[i] = ms;
+    }
+  }
+  *calls = (int32_t)n;
   return KSORT_OK;
 }
 

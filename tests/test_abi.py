@@ -60,6 +60,9 @@ def test_host_side_rejections_need_no_gpu(lib):
     assert lib.ksort_selftest_wait_timeout(0, None) == 1
     assert lib.ksort_partition_out_noalloc(0, None, None, (1 << 24) + 1, None, None) == 9
     assert lib.ksort_partition_out_noalloc(0, None, None, 0, None, None) == 1
+    assert lib.ksort_get_phase_times(None, 1, None, None) == 1  # no output buffers
+    assert lib.ksort_get_phase_times(None, -1, None, None) == 1
+    assert lib.ksort_set_phase_timing(0) == 0
 
 
 def test_tuning_validation(lib):
