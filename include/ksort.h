@@ -71,15 +71,20 @@ KSORT_API ksort_status_t ksort_partition(ksort_dtype_t dtype, void *keys_dev, in
                                int64_t *key_index_dev, ksort_stream_t stream);
 
 /* The same partition, out of place: in_dev is read, out_dev (n keys, not overlapping
- * in_dev) receives the partitioned keys. Tile shapes 1-9: one launch, one read and one
- * write pass over the keys: CTAs take the tiles round-robin, stage each next tile into
- * shared memory by a bulk copy, chain the tiles' less counts by decoupled look-back, and
- * write each tile's two sides to the front and the back of out_dev. Tile shapes 10-12
- * (the wave form): two launches with no waits between CTAs: every warp counts the less
- * keys of its run of warp tiles, then (under programmatic dependent launch) moves them
- * with the prefix of those counts; the keys are read twice. The CTA shape is that of the
- * tuned tile_shape (see ksort_set_tuning); the order within each side differs between
- * forms, the key index and the two sides' contents do not. */
+ * in_dev) receives the partitioned keys. The default form (the tuning's partition_form
+ * 1-4, see ksort_partition_shape) is one launch that reads and writes every key once:
+ * CTAs claim tiles in ascending order and stage them into shared memory by bulk copies;
+ * data warps compact each tile there (less keys from the front, >= keys from the back)
+ * and publish its less count; one warp per CTA adds, to the CTA's own running count, the
+ * counts of the tiles that other CTAs claimed in between, which gives the tile's global
+ * offsets; the data warps then write both runs with 128-bit stores.
+ * With partition_form -1 the form follows tile_shape instead. Tile shapes 1-9: one launch
+ * (CTAs take the tiles round-robin and chain their less counts by decoupled look-back).
+ * Tile shapes 10-12 (the wave form): two launches with no waits between CTAs: every warp
+ * counts the less keys of its run of warp tiles, then (under programmatic dependent
+ * launch) moves them with the prefix of those counts; the keys are read twice. The order
+ * within each side differs between forms, the key index and the two sides' contents do
+ * not. */
 KSORT_API ksort_status_t ksort_partition_out(ksort_dtype_t dtype, const void *in_dev, void *out_dev,
                                    int64_t n, int64_t *key_index_dev, ksort_stream_t stream);
 
@@ -205,6 +210,9 @@ KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t ma
  *                  sub-array of 2 .. medium_tiles tile passes is taken by one CTA, which
  *                  counts every tile first and then moves them with the prefixes it
  *                  knows (no look-back); 1 .. 16, -1 = off (the default).
+ *   partition_form: single partitions (ksort_partition, ksort_partition_out): 1 .. 4 the
+ *                  one-pass ring partition in that configuration (1 = the default, see
+ *                  ksort_partition_shape); -1 = the form that tile_shape names.
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
@@ -213,6 +221,7 @@ typedef struct {
     int32_t tile_shape;
     int32_t wave_levels;
     int32_t medium_tiles;
+    int32_t partition_form;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);
@@ -238,6 +247,14 @@ KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
  *                     form 0. Single partitions: see ksort_partition_out. */
 KSORT_API ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
                                           int32_t *keys_per_thread, int32_t *form);
+
+/* Configuration `form` (1 .. 4) of the one-pass ring partition for `dtype`: CTAs of
+ * *threads threads (one producer warp, one look-back warp, the rest data warps) that
+ * stage tiles of *tile_keys keys, compiled for *ctas_per_sm CTAs per SM. Every
+ * configuration moves the same bytes per tile for 4- and 8-byte keys. */
+KSORT_API ksort_status_t ksort_partition_shape(ksort_dtype_t dtype, int32_t form,
+                                               int32_t *threads, int32_t *tile_keys,
+                                               int32_t *ctas_per_sm);
 
 /* Failure-path check: runs one device-side wait, of the kind the partition's look-back
  * uses, on a flag that nothing ever sets. The wait gives up after limit_ms (1..60000),

@@ -24,7 +24,7 @@ __all__ = [
     "ksort_get_stats", "ksort_set_phase_timing", "ksort_get_phase_times",
     "ksort_get_phase_history",
     "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
-    "ksort_tile_keys", "ksort_tile_shape", "ksort_status_string", "ksort_last_cuda_error",
+    "ksort_tile_keys", "ksort_tile_shape", "ksort_partition_shape", "ksort_status_string", "ksort_last_cuda_error",
     "ksort_selftest_wait_timeout", "ksort_debug_trace",
     "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
 ]
@@ -62,7 +62,8 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("spin_limit_ms", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
-                ("wave_levels", ctypes.c_int32), ("medium_tiles", ctypes.c_int32)]
+                ("wave_levels", ctypes.c_int32), ("medium_tiles", ctypes.c_int32),
+                ("partition_form", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -108,6 +109,9 @@ def load():
             "ksort_tile_shape": (i32, [i32, i32, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]),
+            "ksort_partition_shape": (i32, [i32, i32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
             "ksort_status_string": (ctypes.c_char_p, [i32]),
             "ksort_last_cuda_error": (ctypes.c_char_p, []),
             "ksort_selftest_wait_timeout": (i32, [i32, vp]),
@@ -242,10 +246,13 @@ def ksort_get_phase_times(stream=None) -> list:
 
 
 def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0,
-                     tile_shape: int = 0, wave_levels: int = 0, medium_tiles: int = 0):
+                     tile_shape: int = 0, wave_levels: int = 0, medium_tiles: int = 0,
+                     partition_form: int = 0):
     """Zero arguments keep their value; ctas_per_sm=-1 restores "as many as fit",
-    wave_levels=-1 the automatic level count, medium_tiles=-1 turns whole-item CTAs off."""
-    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape, wave_levels, medium_tiles)
+    wave_levels=-1 the automatic level count, medium_tiles=-1 turns whole-item CTAs off,
+    partition_form=-1 makes single partitions follow tile_shape instead of the ring."""
+    t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape, wave_levels, medium_tiles,
+               partition_form)
     _check(load().ksort_set_tuning(dtype, ctypes.byref(t)), "ksort_set_tuning")
 
 
@@ -254,7 +261,7 @@ def ksort_get_tuning(dtype: int) -> dict:
     _check(load().ksort_get_tuning(dtype, ctypes.byref(t)), "ksort_get_tuning")
     return {"cutoff": t.cutoff, "ctas_per_sm": t.ctas_per_sm, "spin_limit_ms": t.spin_limit_ms,
             "tile_shape": t.tile_shape, "wave_levels": t.wave_levels,
-            "medium_tiles": t.medium_tiles}
+            "medium_tiles": t.medium_tiles, "partition_form": t.partition_form}
 
 
 def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
@@ -264,6 +271,14 @@ def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
     _check(load().ksort_tile_shape(dtype, shape, ctypes.byref(nt), ctypes.byref(ipt),
                                    ctypes.byref(fm)), "ksort_tile_shape")
     return int(nt.value), int(ipt.value), int(fm.value)
+
+
+def ksort_partition_shape(dtype: int, form: int) -> tuple[int, int, int]:
+    """(threads, tile keys, CTAs per SM) of ring-partition configuration `form` (1-4)."""
+    nt, tk, occ = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().ksort_partition_shape(dtype, form, ctypes.byref(nt), ctypes.byref(tk),
+                                        ctypes.byref(occ)), "ksort_partition_shape")
+    return int(nt.value), int(tk.value), int(occ.value)
 
 
 def ksort_max_cutoff(dtype: int) -> int:

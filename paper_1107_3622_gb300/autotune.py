@@ -2,7 +2,8 @@
 or a single partition), the form of the partition passes (kernel kind and threads x
 keys per thread), the number of level-synchronous levels when that form is the wave
 form, the shared-memory cutoff below which sub-arrays are finished in SMEM, and the
-finisher's CTAs per SM.
+finisher's CTAs per SM. For a single partition it picks the configuration of the ring
+partition (tile size, slots, CTAs per SM), or the tile shape's own form if that wins.
 
 Every candidate runs the real workload through the C ABI on the current device. The
 input is restored from a pristine copy and L2 flushed before each timed run, and CUDA
@@ -34,6 +35,8 @@ WAVE_SHAPES = (10, 11, 12)
 # -1: the library's automatic count; fixed counts around the depth of random inputs
 WAVE_LEVELS = (-1, 6, 9, 12, 15, 18)
 FINISHER_CTAS = (-1, 3, 2)
+# single partitions: the ring partition's configurations, or -1 (the tile shape's form)
+PARTITION_FORMS = (1, 2, 3, 4, -1)
 _L2_FLUSH_BYTES = 256 << 20
 _lock = threading.Lock()
 
@@ -100,7 +103,8 @@ def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None) -> dict | None
         return None
     t = e["tuning"]
     ksort_set_tuning(dtype, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
-                     tile_shape=t["tile_shape"], wave_levels=t.get("wave_levels", -1))
+                     tile_shape=t["tile_shape"], wave_levels=t.get("wave_levels", -1),
+                     partition_form=t.get("partition_form", 1))
     return e
 
 
@@ -193,28 +197,35 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
     cutoffs = [c for c in CUTOFFS if c <= maxc]
     best = {"tile_shape": before["tile_shape"], "cutoff": before["cutoff"],
             "ctas_per_sm": before["ctas_per_sm"] or -1,
-            "wave_levels": before.get("wave_levels", -1)}
+            "wave_levels": before.get("wave_levels", -1),
+            "partition_form": before.get("partition_form", 1)}
     tried = {}
 
     def measure(cfg) -> float:
         if cfg["tile_shape"] not in WAVE_SHAPES:
             cfg["wave_levels"] = -1  # no effect outside the wave form
-        key = (cfg["tile_shape"], cfg["cutoff"], cfg["ctas_per_sm"], cfg["wave_levels"])
+        key = (cfg["tile_shape"], cfg["cutoff"], cfg["ctas_per_sm"], cfg["wave_levels"],
+               cfg["partition_form"])
         if key not in tried:
             ksort_set_tuning(dtype, cutoff=cfg["cutoff"], ctas_per_sm=cfg["ctas_per_sm"],
-                             tile_shape=cfg["tile_shape"], wave_levels=cfg["wave_levels"])
+                             tile_shape=cfg["tile_shape"], wave_levels=cfg["wave_levels"],
+                             partition_form=cfg["partition_form"])
             tried[key] = runner.time(reps)
         return tried[key]
 
     best_ms = measure(best)
     axes = (("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS), ("cutoff", cutoffs),
             ("ctas_per_sm", FINISHER_CTAS))
-    if kind == "partition":  # part_kernel or the split pair: only the CTA shape matters
-        axes = (("tile_shape", SHAPES[:3] + WAVE_SHAPES),)
+    if kind == "partition":
+        # the ring partition's configuration; the CTA shape only matters for the tile
+        # shape's own forms (part_kernel or the split pair), under partition_form -1
+        axes = (("partition_form", PARTITION_FORMS), ("tile_shape", SHAPES[:3] + WAVE_SHAPES))
     for _ in range(max_rounds):
         improved = False
         for name, values in axes:
             if name == "wave_levels" and best["tile_shape"] not in WAVE_SHAPES:
+                continue
+            if kind == "partition" and name == "tile_shape" and best["partition_form"] != -1:
                 continue
             for v in values:
                 cfg = dict(best, **{name: v})
@@ -224,16 +235,18 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
         if not improved:
             break
     ksort_set_tuning(dtype, cutoff=best["cutoff"], ctas_per_sm=best["ctas_per_sm"],
-                     tile_shape=best["tile_shape"], wave_levels=best["wave_levels"])
+                     tile_shape=best["tile_shape"], wave_levels=best["wave_levels"],
+                     partition_form=best["partition_form"])
     if not runner.check_sorted():
         ksort_set_tuning(dtype, cutoff=before["cutoff"], ctas_per_sm=before["ctas_per_sm"] or -1,
-                         tile_shape=before["tile_shape"], wave_levels=before.get("wave_levels", -1))
+                         tile_shape=before["tile_shape"], wave_levels=before.get("wave_levels", -1),
+                         partition_form=before.get("partition_form", 1))
         raise RuntimeError("autotuned configuration produced an unsorted output")
     entry = {"workload": workload_key(kind, dtype, n, lengths), "device": device_key(),
              "library": library_hash(), "tuning": best, "ms": round(best_ms, 4),
              "keys": runner.total, "reps": reps,
              "candidates": [{"tile_shape": k[0], "cutoff": k[1], "ctas_per_sm": k[2],
-                             "wave_levels": k[3], "ms": round(v, 4)}
+                             "wave_levels": k[3], "partition_form": k[4], "ms": round(v, 4)}
                             for k, v in sorted(tried.items())]}
     if use_cache:
         _store(_full_key(kind, dtype, n, lengths), entry)
@@ -242,6 +255,7 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 
 def reset(dtype: int):
     """Back to the library defaults (tile shape 1, default cutoff, all finisher CTAs,
-    automatic wave levels)."""
+    automatic wave levels, ring partition configuration 1)."""
     default_cutoff = {F32: 4096, F64: 2048, U32: 4096}[dtype]
-    ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1, wave_levels=-1)
+    ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1, wave_levels=-1,
+                     partition_form=1)

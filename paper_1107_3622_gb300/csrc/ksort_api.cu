@@ -51,6 +51,9 @@ struct Ops {
   cudaError_t (*wave_level)(const SortParams &, int, int, int, bool, cudaStream_t);
   cudaError_t (*wave_handoff)(const SortParams &, int, int, bool, cudaStream_t);
   cudaError_t (*partition_split)(const SortParams &, int, int, cudaStream_t);
+  RingInfo (*ring_info)(int);
+  cudaError_t (*ring_occupancy)(int, int *);
+  cudaError_t (*ring_partition)(const SortParams &, int, int, cudaStream_t);
 };
 
 template <typename K>
@@ -60,7 +63,8 @@ Ops ops_for() {
              &Launcher<K>::tile_count, &Launcher<K>::part_occupancy,   &Launcher<K>::partition,
              &Launcher<K>::exact_work_bytes, &Launcher<K>::exact,
              &Launcher<K>::wave_occupancy, &Launcher<K>::wave_level, &Launcher<K>::wave_handoff,
-             &Launcher<K>::partition_split};
+             &Launcher<K>::partition_split,
+             &Launcher<K>::ring_info,  &Launcher<K>::ring_occupancy, &Launcher<K>::ring_partition};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -76,13 +80,14 @@ struct Tuning {
   int variant;      // tile shape of the tile passes, 0 .. kTileVariants - 1
   int wave_levels;  // wave form: level-synchronous levels; 0: automatic
   int medium_tiles; // register-form queue: largest item one CTA takes whole; 0: off
+  int part_form;    // single partitions: ring configuration 1 .. kRingConfigs; 0: tile shape's form
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0}, {2048, 0, 2000, 0, 0, 0},
-                      {4096, 0, 2000, 0, 0, 0}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1}, {2048, 0, 2000, 0, 0, 0, 1},
+                      {4096, 0, 2000, 0, 0, 0, 1}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -353,6 +358,23 @@ ksort_status_t part_occupancy(ksort_dtype_t dt, int shape, int *occ) {
   return KSORT_OK;
 }
 
+std::map<std::pair<int, int>, int> g_ring_occ;  // (dtype, configuration) -> CTAs per SM
+
+ksort_status_t ring_occupancy(ksort_dtype_t dt, int cfg, int *occ) {
+  auto key = std::make_pair((int)dt, cfg);
+  auto it = g_ring_occ.find(key);
+  if (it != g_ring_occ.end()) {
+    *occ = it->second;
+    return KSORT_OK;
+  }
+  int o = 0;
+  KS_CUDA(ops(dt).ring_occupancy(cfg, &o));
+  if (o < 1) return KSORT_ERR_INTERNAL;
+  g_ring_occ[key] = o;
+  *occ = o;
+  return KSORT_OK;
+}
+
 SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
   SortParams p{};
   p.keys = keys;
@@ -411,16 +433,27 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
     if (!in_place) KS_CUDA(cudaMemcpyAsync(dst, in, kb, cudaMemcpyDeviceToDevice, s));
     return KSORT_OK;
   }
-  // One launch of part_kernel (the CTA shape of the tuned form), or for the wave form the
-  // count and move launches of the split partition: buffer 0 is read, buffer 1 receives
-  // the result.
+  // One launch of part_ring_kernel (the tuned configuration); or, with the ring turned
+  // off, one launch of part_kernel (the CTA shape of the tuned form) or for the wave form
+  // the count and move launches of the split partition. Buffer 0 is read, buffer 1
+  // receives the result.
   const int shape = tu.variant % kTileShapes;
-  const long long tiles = ops(dt).tile_count(shape, in, 0, n);  // form-0 variants: plain tiles
-  if ((unsigned long long)tiles > ws->lb_cap) return KSORT_ERR_INVALID_ARG;
-  int occ = 0;
-  if ((st = part_occupancy(dt, shape, &occ)) != KSORT_OK) return st;
   int sms = 0;
   if ((st = device_sms(dev, &sms)) != KSORT_OK) return st;
+  long long tiles = 0;
+  int occ = 0;
+  if (tu.part_form > 0) {
+    const long long tk = ops(dt).ring_info(tu.part_form).tile_keys;
+    // tiles start at the 16-byte boundary at or below element 1 (tile_base)
+    const long long mis = (long long)((reinterpret_cast<uintptr_t>(in) + kb) & 15u) / (long long)kb;
+    const long long base = 1 - mis;
+    tiles = (n - base + tk - 1) / tk;
+    if ((st = ring_occupancy(dt, tu.part_form, &occ)) != KSORT_OK) return st;
+  } else {
+    tiles = ops(dt).tile_count(shape, in, 0, n);  // form-0 variants: plain tiles
+    if ((st = part_occupancy(dt, shape, &occ)) != KSORT_OK) return st;
+  }
+  if ((unsigned long long)tiles > ws->lb_cap) return KSORT_ERR_INVALID_ARG;
   const int grid = (int)std::max<long long>(1, std::min<long long>((long long)sms * occ, tiles));
   SortParams p = sort_params(*ws, const_cast<void *>(in), tu);
   p.scratch = dst;
@@ -433,7 +466,10 @@ ksort_status_t partition_impl(ksort_dtype_t dt, const void *in, void *out, int64
   PhaseMarks pm;
   if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
   KS_CUDA(pm.mark());
-  if (ops(dt).info(tu.variant).form == kWaveForm) {
+  if (tu.part_form > 0) {
+    KS_CUDA(ops(dt).ring_partition(p, tu.part_form, grid, s));
+    ws->launches = 1;
+  } else if (ops(dt).info(tu.variant).form == kWaveForm) {
     KS_CUDA(ops(dt).partition_split(p, shape, sms, s));
     ws->launches = 2;
   } else {
@@ -856,6 +892,18 @@ ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *thr
   return KSORT_OK;
 }
 
+ksort_status_t ksort_partition_shape(ksort_dtype_t dtype, int32_t form, int32_t *threads,
+                                     int32_t *tile_keys, int32_t *ctas_per_sm) {
+  if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (form < 1 || form > kRingConfigs || !threads || !tile_keys || !ctas_per_sm)
+    return KSORT_ERR_INVALID_ARG;
+  const RingInfo ri = ops(dtype).ring_info(form);
+  *threads = ri.block;
+  *tile_keys = ri.tile_keys;
+  *ctas_per_sm = ri.min_blocks;
+  return KSORT_OK;
+}
+
 ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
   if (!t) return KSORT_ERR_INVALID_ARG;
@@ -866,6 +914,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->tile_shape < 0 || t->tile_shape > kTileVariants) return KSORT_ERR_INVALID_ARG;
   if (t->wave_levels < -1 || t->wave_levels > 64) return KSORT_ERR_INVALID_ARG;
   if (t->medium_tiles < -1 || t->medium_tiles > kMediumMaxTiles) return KSORT_ERR_INVALID_ARG;
+  if (t->partition_form < -1 || t->partition_form > kRingConfigs) return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
@@ -874,6 +923,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->tile_shape) g.variant = t->tile_shape - 1;
   if (t->wave_levels) g.wave_levels = t->wave_levels < 0 ? 0 : t->wave_levels;
   if (t->medium_tiles) g.medium_tiles = t->medium_tiles < 0 ? 0 : t->medium_tiles;
+  if (t->partition_form) g.part_form = t->partition_form < 0 ? 0 : t->partition_form;
   return KSORT_OK;
 }
 
@@ -888,6 +938,7 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->tile_shape = g.variant + 1;
   out->wave_levels = g.wave_levels ? g.wave_levels : -1;
   out->medium_tiles = g.medium_tiles ? g.medium_tiles : -1;
+  out->partition_form = g.part_form ? g.part_form : -1;
   return KSORT_OK;
 }
 

@@ -53,7 +53,13 @@ struct alignas(128) Control {
   // single-partition kernel: CTAs finished, and its own stop flag (both back to 0 when
   // the last CTA of a call finishes)
   unsigned part_done, part_abort;
-  unsigned long long pad1[2];
+  unsigned long long part_ticket;  // ring partition: tiles claimed (0 between calls)
+  // ring partition: CTAs finished (0 between calls), and the generation of the last call
+  // that stopped on an error (never cleared)
+  unsigned ring_done, ring_abort;
+  // ring partition, reservation form: (>= keys << 32) | less keys of the tiles that have
+  // taken their output ranges so far (0 between calls)
+  unsigned long long ring_resv;
   // level-synchronous passes: per level parity, items << kWaveKeyBits | classified keys
   unsigned long long wave_ctr[2];
   unsigned long long wave_fin;  // keys of an even level waiting for their final index
@@ -140,6 +146,16 @@ struct KernelInfo {
   int form;           // 0 tile_kernel, 1 tile_pipe_kernel, 2 tile_ws_kernel, 3 wave
 };
 
+// One compiled configuration of the ring partition (part_ring_kernel).
+constexpr int kRingConfigs = 4;
+struct RingInfo {
+  int block;        // threads per CTA (producer warp, look-back warp, data warps)
+  int tile_keys;    // keys per tile
+  int min_blocks;   // CTAs per SM the kernel is compiled for
+  int data_warps;
+  int keys_per_lane;
+};
+
 template <typename K>
 struct Launcher {
   static KernelInfo info(int variant);
@@ -152,6 +168,10 @@ struct Launcher {
   // single partitions: part_kernel with CTA shape `shape` (0 .. kTileShapes - 1)
   static cudaError_t part_occupancy(int shape, int *ctas);
   static cudaError_t partition(const SortParams &p, int shape, int grid, cudaStream_t s);
+  // single partitions: part_ring_kernel in configuration `cfg` (1 .. kRingConfigs)
+  static RingInfo ring_info(int cfg);
+  static cudaError_t ring_occupancy(int cfg, int *ctas);
+  static cudaError_t ring_partition(const SortParams &p, int cfg, int grid, cudaStream_t s);
   // Steps 1-4 in the paper's element order (exact layout), n >= 2; `work` holds
   // exact_work_bytes(n) bytes of device scratch.
   static size_t exact_work_bytes(long long n);

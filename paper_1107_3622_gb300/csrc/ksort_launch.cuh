@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "ksort_device.cuh"
+#include "ksort_part_ring.cuh"
 
 namespace ksort {
 
@@ -175,6 +176,80 @@ cudaError_t Launcher<K>::partition(const SortParams &p, int shape, int grid, cud
     cudaError_t e = part_kernel_of<K, S>(&fn, &smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, S::NT, smem, st>>>(p);
+    return cudaGetLastError();
+  });
+}
+
+// ------------------------------------------------------------------ ring partition
+// Compiled configurations of part_ring_kernel (1-based, as in ksort_tuning_t): data
+// warps x keys per lane (the tile), slots, CTAs per SM, look-back window of 32 x PER
+// descriptors, look-back warps (0: the reservation form; otherwise the ordered form), and
+// the tiles a CTA may have loading or awaiting compaction (measured: 3, 4 and 6 equal at
+// 5e7 keys, 2 slower) (about the number of CTAs, so that the tiles claimed between two of a
+// CTA's own are usually read in one round trip). 8-byte keys take half the keys per
+// lane, so every configuration stages the same bytes.
+template <typename K, int C>
+struct RingOf;
+template <typename K> struct RingOf<K, 1> {  // reservation: 16 KiB tiles, 6 slots, 2 CTAs per SM
+  using Cfg = dev::RingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 12, 0, 3>;
+};
+template <typename K> struct RingOf<K, 2> {  // reservation: 8 KiB tiles, 8 slots, 3 CTAs per SM
+  using Cfg = dev::RingCfg<K, 8, 32 / (int)sizeof(K), 8, 3, 10, 0, 3>;
+};
+template <typename K> struct RingOf<K, 3> {  // reservation: 32 KiB tiles, 6 slots, 1 CTA per SM
+  using Cfg = dev::RingCfg<K, 16, 64 / (int)sizeof(K), 6, 1, 6, 0, 3>;
+};
+template <typename K> struct RingOf<K, 4> {  // ordered: 16 KiB tiles, 6 slots, 2 CTAs per SM, 2 look-back warps
+  using Cfg = dev::RingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 12, 2, 3>;
+};
+
+template <typename K, typename F>
+decltype(auto) with_ring(int c, F &&f) {
+  switch (c) {
+    case 2: return f(typename RingOf<K, 2>::Cfg{});
+    case 3: return f(typename RingOf<K, 3>::Cfg{});
+    case 4: return f(typename RingOf<K, 4>::Cfg{});
+    default: return f(typename RingOf<K, 1>::Cfg{});
+  }
+}
+
+template <typename K, typename C>
+cudaError_t ring_kernel_of(void (**fn)(SortParams)) {
+  *fn = dev::part_ring_kernel<K, C::NDW, C::IPT, C::S, C::MINB, C::PER, C::NLB, C::DEPTH>;
+  cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
+}
+
+template <typename K>
+RingInfo Launcher<K>::ring_info(int cfg) {
+  return with_ring<K>(cfg, [](auto c) {
+    using C = decltype(c);
+    return RingInfo{C::NT, C::TILE, C::MINB, C::NDW, C::IPT};
+  });
+}
+
+template <typename K>
+cudaError_t Launcher<K>::ring_occupancy(int cfg, int *ctas) {
+  return with_ring<K>(cfg, [&](auto c) {
+    using C = decltype(c);
+    void (*fn)(SortParams) = nullptr;
+    cudaError_t e = ring_kernel_of<K, C>(&fn);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, C::NT, C::SMEM);
+  });
+}
+
+template <typename K>
+cudaError_t Launcher<K>::ring_partition(const SortParams &p, int cfg, int grid, cudaStream_t st) {
+  return with_ring<K>(cfg, [&](auto c) {
+    using C = decltype(c);
+    void (*fn)(SortParams) = nullptr;
+    cudaError_t e = ring_kernel_of<K, C>(&fn);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, C::NT, C::SMEM, st>>>(p);
     return cudaGetLastError();
   });
 }

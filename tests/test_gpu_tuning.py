@@ -27,7 +27,7 @@ def restore(ks):
     yield
     for c, t in saved.items():
         ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
-                            tile_shape=t["tile_shape"])
+                            tile_shape=t["tile_shape"], partition_form=t["partition_form"])
 
 
 def _sort(ks, a):
@@ -49,7 +49,8 @@ def _oracle(ref, a):
 def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
     import torch
     code = DTYPES[dtype]
-    ks.ksort_set_tuning(code, tile_shape=shape)
+    # single partitions follow the tile shape (part_kernel or the split partition)
+    ks.ksort_set_tuning(code, tile_shape=shape, partition_form=-1)
     nt, ipt, form = ks.ksort_tile_shape(code, shape)
     tile = (nt - 64 if form == 2 else nt) * ipt
     assert ks.ksort_tile_keys(code) == tile
@@ -117,8 +118,13 @@ def test_autotuner_partition_kind(ks, restore, tmp_path, monkeypatch):
     monkeypatch.setenv("KSORT_TUNE_CACHE", str(tmp_path / "tune.json"))
     e = autotune.autotune("partition", ks.F32, n=500_000, reps=2, max_rounds=1)
     assert e["workload"] == "partition:f32:2^19"
-    # only the form of the tile passes is searched for a single partition
+    # only the form of the partition is searched for a single partition
     assert {c["cutoff"] for c in e["candidates"]} == {e["tuning"]["cutoff"]}
-    # the three CTA shapes of part_kernel and of the split partition (the wave form)
-    assert sorted(c["tile_shape"] for c in e["candidates"]) == [1, 2, 3, 10, 11, 12]
-    assert ks.ksort_get_tuning(ks.F32)["tile_shape"] == e["tuning"]["tile_shape"]
+    # every ring configuration, and the tile shape's own form (-1)
+    assert {c["partition_form"] for c in e["candidates"]} == set(autotune.PARTITION_FORMS)
+    if e["tuning"]["partition_form"] == -1:
+        # then the three CTA shapes of part_kernel and of the split partition
+        assert {c["tile_shape"] for c in e["candidates"]} >= {1, 2, 3, 10, 11, 12}
+    t = ks.ksort_get_tuning(ks.F32)
+    assert t["partition_form"] == e["tuning"]["partition_form"]
+    assert t["tile_shape"] == e["tuning"]["tile_shape"]

@@ -29,11 +29,16 @@ def ks():
 
 @pytest.fixture
 def restore(ks):
+    """Single partitions in this module follow the tile shape (the split partition for
+    the wave form, part_kernel for shapes 1-3) instead of the ring partition."""
     saved = {c: ks.ksort_get_tuning(c) for c in DTYPES.values()}
+    for c in DTYPES.values():
+        ks.ksort_set_tuning(c, partition_form=-1)
     yield
     for c, t in saved.items():
         ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
-                            tile_shape=t["tile_shape"], wave_levels=t["wave_levels"])
+                            tile_shape=t["tile_shape"], wave_levels=t["wave_levels"],
+                            partition_form=t["partition_form"])
 
 
 def _dev(a):
@@ -169,6 +174,10 @@ def test_wave_stats_and_bad_offsets(ks, restore):
     ks.ksort_set_tuning(ks.F32, tile_shape=10)
     ks.partition_(t)
     assert ks.ksort_get_stats()["launches"] == 2
+    ks.ksort_set_tuning(ks.F32, partition_form=1)  # the ring partition: one launch
+    ks.partition_(t)
+    assert ks.ksort_get_stats()["launches"] == 1
+    ks.ksort_set_tuning(ks.F32, partition_form=-1)
     flat = _dev(gen.uniform_f32(1, 10_000))
     bad = _dev(np.array([0, 6000, 4000, 10_000], np.int64))
     ks.sort_batched_(flat, bad)

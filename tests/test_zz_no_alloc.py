@@ -1,7 +1,10 @@
 """ksort_partition_out_noalloc: the partition of Steps 1-4 (Section 1.1) with the kernels'
-scratch in one fixed device array, so that a call allocates nothing. Its results must
-equal those of ksort_partition_out (the same kernels on a per-stream workspace) and the
-oracle's key index, on two calls in a row that share the array.
+scratch in one fixed device array, so that a call allocates nothing. It runs the sort's
+seed kernel and tile_kernel (tile shape 1, whatever the tuning) and a status kernel:
+three launches. Its results are checked against ksort_partition_out on two calls in a row
+that share the array: the oracle's key index and the same two sides (as multisets, the
+partition's contract) against the default form, and byte for byte against the form that
+follows tile shape 1 (part_kernel), which lays tiles out the way tile_kernel does.
 
 This file is collected last on purpose. It must pass in a fresh process, where its first
 call does the per-device set-up, and after every other test has used the library."""
@@ -46,10 +49,28 @@ def _oracle_index(ref, a):
     return i
 
 
+def _same_sides(got, want, i):
+    """Same key at i and the same multisets on both sides of it."""
+    return got[i:i + 1].tobytes() == want[i:i + 1].tobytes() and \
+        np.sort(got[:i]).tobytes() == np.sort(want[:i]).tobytes() and \
+        np.sort(got[i + 1:]).tobytes() == np.sort(want[i + 1:]).tobytes()
+
+
+@pytest.fixture
+def tile_layout_form(ks):
+    """ksort_partition_out under partition_form -1 and tile shape 1 runs part_kernel,
+    whose tiles have tile_kernel's layout; the tuning is restored afterwards."""
+    saved = {c: ks.ksort_get_tuning(c) for c in (ks.F32, ks.F64, ks.U32)}
+    yield lambda code: ks.ksort_set_tuning(code, partition_form=-1, tile_shape=1)
+    for c, t in saved.items():
+        ks.ksort_set_tuning(c, partition_form=t["partition_form"], tile_shape=t["tile_shape"])
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
-def test_two_calls_in_a_row_match_partition_out(ref, ks, dtype):
+def test_two_calls_in_a_row_match_partition_out(ref, ks, tile_layout_form, dtype):
     """Two back-to-back calls on one stream (the second smaller than the first, with a
-    misaligned start), then the same two inputs through ksort_partition_out."""
+    misaligned start), then the same two inputs through ksort_partition_out: the default
+    form (same index and sides) and the tile-layout form (same bytes)."""
     import torch
     code = {"f32": ks.F32, "f64": ks.F64, "u32": ks.U32}[dtype]
     a1 = gen.make("uniform", dtype, 1_000_003, gen.seed_for(5, 1, 0))
@@ -59,37 +80,46 @@ def test_two_calls_in_a_row_match_partition_out(ref, ks, dtype):
     s2 = _dev(big)[1:]
     g1, g2 = _poisoned(s1), _poisoned(s2)
     w1, w2 = _poisoned(s1), _poisoned(s2)
-    idx = torch.full((4,), -99, dtype=torch.int64, device="cuda")
+    b1, b2 = _poisoned(s1), _poisoned(s2)
+    idx = torch.full((6,), -99, dtype=torch.int64, device="cuda")
     ks.ksort_partition_out_noalloc(code, s1, g1, a1.size, idx[0:1])
     ks.ksort_partition_out_noalloc(code, s2, g2, a2.size, idx[1:2])
     ks.ksort_partition_out(code, s1, w1, a1.size, idx[2:3])
     ks.ksort_partition_out(code, s2, w2, a2.size, idx[3:4])
+    tile_layout_form(code)
+    ks.ksort_partition_out(code, s1, b1, a1.size, idx[4:5])
+    ks.ksort_partition_out(code, s2, b2, a2.size, idx[5:6])
     torch.cuda.synchronize()
     assert ks.ksort_get_device_error() == 0
-    i1, i2, j1, j2 = idx.tolist()
-    assert (i1, i2) == (j1, j2)
+    i1, i2, j1, j2, k1, k2 = idx.tolist()
+    assert (i1, i2) == (j1, j2) == (k1, k2)
     assert i1 == _oracle_index(ref, a1) and i2 == _oracle_index(ref, a2)
-    assert _host(g1).tobytes() == _host(w1).tobytes()
-    assert _host(g2).tobytes() == _host(w2).tobytes()
+    assert _same_sides(_host(g1), _host(w1), i1)
+    assert _same_sides(_host(g2), _host(w2), i2)
+    assert _host(g1).tobytes() == _host(b1).tobytes()
+    assert _host(g2).tobytes() == _host(b2).tobytes()
     assert _host(s1).tobytes() == a1.tobytes()  # inputs untouched
     assert _host(s2).tobytes() == a2.tobytes()
 
 
-def test_largest_size_and_one_key(ref, ks):
+def test_largest_size_and_one_key(ref, ks, tile_layout_form):
     """n = KSORT_NOALLOC_MAX_KEYS float64 keys from a start that is not tile-aligned
     (the most tile tickets the fixed array must hold), then n = 1."""
     import torch
     n = ks.KSORT_NOALLOC_MAX_KEYS
     big = gen.make("uniform", "f64", n + 1, gen.seed_for(5, 3, 0))
     src = _dev(big)[1:]
-    got, want = _poisoned(src), _poisoned(src)
-    idx = torch.full((2,), -99, dtype=torch.int64, device="cuda")
+    got, want, same = _poisoned(src), _poisoned(src), _poisoned(src)
+    idx = torch.full((3,), -99, dtype=torch.int64, device="cuda")
     ks.ksort_partition_out_noalloc(ks.F64, src, got, n, idx[0:1])
     ks.ksort_partition_out(ks.F64, src, want, n, idx[1:2])
+    tile_layout_form(ks.F64)
+    ks.ksort_partition_out(ks.F64, src, same, n, idx[2:3])
     torch.cuda.synchronize()
-    i, j = idx.tolist()
-    assert i == j == _oracle_index(ref, big[1:])
-    assert torch.equal(got.view(torch.int64), want.view(torch.int64))
+    i, j, k = idx.tolist()
+    assert i == j == k == _oracle_index(ref, big[1:])
+    assert _same_sides(_host(got), _host(want), i)
+    assert torch.equal(got.view(torch.int64), same.view(torch.int64))
     one_in = _dev(np.array([0.25], np.float64))
     one_out = _poisoned(one_in)
     ks.ksort_partition_out_noalloc(ks.F64, one_in, one_out, 1, idx[0:1])
