@@ -213,6 +213,13 @@ KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t ma
  *   partition_form: single partitions (ksort_partition, ksort_partition_out): 1 .. 4 the
  *                  one-pass ring partition in that configuration (1 = the default, see
  *                  ksort_partition_shape); -1 = the form that tile_shape names.
+ *   sort_reserve:  sorts in tile shapes 1 .. 3 and 10 .. 12: 1 (the default) = each tile
+ *                  pass takes its output ranges in its sub-array with one atomic add on
+ *                  the sub-array's counter, so no tile waits for another; the order of
+ *                  the tiles' runs inside each side then follows the order in which the
+ *                  tiles finished (the sorted result does not change; only which key heads
+ *                  each later sub-array does). -1 = decoupled look-back in tile order
+ *                  (the layout depends on the input alone).
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
@@ -222,6 +229,7 @@ typedef struct {
     int32_t wave_levels;
     int32_t medium_tiles;
     int32_t partition_form;
+    int32_t sort_reserve;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);

@@ -81,13 +81,14 @@ struct Tuning {
   int wave_levels;  // wave form: level-synchronous levels; 0: automatic
   int medium_tiles; // register-form queue: largest item one CTA takes whole; 0: off
   int part_form;    // single partitions: ring configuration 1 .. kRingConfigs; 0: tile shape's form
+  int reserve;      // sorts, register and wave forms: tile ranges by reservation (else look-back)
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1}, {2048, 0, 2000, 0, 0, 0, 1},
-                      {4096, 0, 2000, 0, 0, 0, 1}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1, 1}, {2048, 0, 2000, 0, 0, 0, 1, 1},
+                      {4096, 0, 2000, 0, 0, 0, 1, 1}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -545,6 +546,7 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     // medium items are served by tile_kernel alone (the register form's queue)
     const int form = ops(dt).info(tu.variant).form;
     p.medium_tiles = form == 0 || form == kWaveForm ? tu.medium_tiles : 0;
+    p.reserve = (form == 0 || form == kWaveForm) && tu.reserve ? 1 : 0;
   }
   p.num_roots = offsets ? num_arrays : 1;
   p.total = total;
@@ -915,6 +917,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->wave_levels < -1 || t->wave_levels > 64) return KSORT_ERR_INVALID_ARG;
   if (t->medium_tiles < -1 || t->medium_tiles > kMediumMaxTiles) return KSORT_ERR_INVALID_ARG;
   if (t->partition_form < -1 || t->partition_form > kRingConfigs) return KSORT_ERR_INVALID_ARG;
+  if (t->sort_reserve < -1 || t->sort_reserve > 1) return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
@@ -924,6 +927,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->wave_levels) g.wave_levels = t->wave_levels < 0 ? 0 : t->wave_levels;
   if (t->medium_tiles) g.medium_tiles = t->medium_tiles < 0 ? 0 : t->medium_tiles;
   if (t->partition_form) g.part_form = t->partition_form < 0 ? 0 : t->partition_form;
+  if (t->sort_reserve) g.reserve = t->sort_reserve > 0 ? 1 : 0;
   return KSORT_OK;
 }
 
@@ -939,6 +943,7 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->wave_levels = g.wave_levels ? g.wave_levels : -1;
   out->medium_tiles = g.medium_tiles ? g.medium_tiles : -1;
   out->partition_form = g.part_form ? g.part_form : -1;
+  out->sort_reserve = g.reserve ? 1 : -1;
   return KSORT_OK;
 }
 

@@ -316,6 +316,12 @@ __device__ __forceinline__ void scatter_keys(K *so, const K (&x)[IPT], unsigned 
   }
 }
 
+// Reserved ranges [lbase, lbase + L) and [gbase, gbase + G) inside the sub-array.
+__device__ __forceinline__ bool ranges_ok(long long begin, long long end, long long lbase,
+                                       unsigned L, long long gbase, unsigned G) {
+  return lbase >= begin && lbase + L <= end && gbase >= begin && gbase + G <= end;
+}
+
 // Global offsets of the two sides of tile t; false (and an error) if inconsistent.
 __device__ __forceinline__ bool tile_dest(long long begin, long long end, long long lo,
                                           unsigned t, unsigned long long E, unsigned L, unsigned G,
@@ -1197,12 +1203,19 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
     }
     unsigned long long *lb = p.lb + it.lb;
     if (tid == 0) {
-      st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));  // aggregate (inclusive: tile 0)
+      if (p.reserve) {
+        // the tile's ranges at once: one add of (>= << 32 | less) to the item's counter
+        // gives the less and >= keys of the tiles that took theirs before
+        sh.E = atomicAdd(&p.ictl[h].less, ((unsigned long long)G << 32) | L);
+        sh.abort = 0;
+      } else {
+        st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));  // aggregate (inclusive: tile 0)
+      }
       trace_mark(p, sh.k, 2);  // loaded and counted
     }
 
     // ---- look-back (warp 0) and scatter (everyone)
-    if (w == 0) {
+    if (w == 0 && !p.reserve) {
       unsigned long long E = 0;
       int status = 0;
       if (t > 0) {
@@ -1234,7 +1247,13 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
 
     // ---- write
     long long lbase = 0, gbase = 0;
-    if (!tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase)) {
+    if (p.reserve) {
+      const long long PL = (long long)(E & 0xffffffffull), PG = (long long)(E >> 32);
+      lbase = it.begin + PL;
+      gbase = it.end - PG - (long long)G;
+    }
+    if (p.reserve ? !(ranges_ok(it.begin, it.end, lbase, L, gbase, G))
+                  : !tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase)) {
       if (tid == 0) raise_error(ctl, kDevInternal, 0x500000000ull | t);
       break;
     }
@@ -1246,7 +1265,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
     if (tid == 0) {
       trace_mark(p, sh.k, 4);  // written
       ++st_tiles;
-      if (t == it.tiles - 1) atomicExch(&p.ictl[h].less, E + L);
+      if (t == it.tiles - 1 && !p.reserve) atomicExch(&p.ictl[h].less, E + L);
       // release: this tile's writes (ordered before by the barrier) and `less` become
       // visible to whichever CTA observes the count reaching tiles
       const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);
@@ -1254,7 +1273,8 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       sh.last = done_before == it.tiles - 1;
       if (sh.last) {
         __threadfence();
-        sh.c_less = ld_acquire(&p.ictl[h].less);
+        const unsigned long long v = ld_acquire(&p.ictl[h].less);
+        sh.c_less = p.reserve ? (v & 0xffffffffull) : v;  // every tile has taken its range
       }
     }
     __syncthreads();
@@ -1624,7 +1644,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(Sort
     if (tid == 0) {
       trace_mark(p, sh.cur.k, 4);
       ++st_tiles;
-      if (t == it.tiles - 1) atomicExch(&p.ictl[h].less, E + L);
+      if (t == it.tiles - 1 && !p.reserve) atomicExch(&p.ictl[h].less, E + L);
       // release: this tile's writes (ordered before by the barrier) and `less` become
       // visible to whichever CTA observes the count reaching tiles
       const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);

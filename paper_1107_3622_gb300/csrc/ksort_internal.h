@@ -91,7 +91,9 @@ struct alignas(16) Item {
 struct alignas(16) ItemCtl {
   unsigned grab;            // tiles handed out
   unsigned done;            // tiles finished
-  unsigned long long less;  // #{x < key} of the item, written by its last tile
+  // #{x < key} of the item, written by its last tile; with reservation, the running
+  // (>= keys << 32) | less keys of the tiles that have taken their ranges
+  unsigned long long less;
 };
 
 struct SortParams {
@@ -123,6 +125,7 @@ struct SortParams {
   unsigned long long *wave_fin;
   int wave;                  // nonzero: the seed queues large roots on the level-0 list
   int medium_tiles;          // items of 2 .. medium_tiles tile passes go to one CTA; 0: off
+  int reserve;               // tile_kernel: output ranges by reservation, not look-back
 };
 constexpr int kTraceWords = 8;
 

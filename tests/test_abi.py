@@ -145,6 +145,14 @@ def test_tile_shapes_and_tuning_fields(lib):
         assert ks.ksort_get_tuning(code)["partition_form"] == 3
         ks.ksort_set_tuning(code, partition_form=before["partition_form"])
         assert ks.ksort_get_tuning(code) == before
+        assert before["sort_reserve"] in (-1, 1)
+        for bad in (-2, 2):
+            with pytest.raises(ks.KSortError):
+                ks.ksort_set_tuning(code, sort_reserve=bad)
+        ks.ksort_set_tuning(code, sort_reserve=-1)
+        assert ks.ksort_get_tuning(code)["sort_reserve"] == -1
+        ks.ksort_set_tuning(code, sort_reserve=before["sort_reserve"])
+        assert ks.ksort_get_tuning(code) == before
         # every ring configuration stages the same bytes per tile for 4- and 8-byte keys
         keyb = 8 if code == ks.F64 else 4
         for form in (1, 2, 3, 4):

@@ -25,12 +25,17 @@ def ks():
 
 @pytest.fixture
 def restore(ks):
+    """Whole-item CTAs lay tiles out as the multi-tile passes do in tile order, so this
+    module compares them under the look-back form of the tile passes (sort_reserve -1),
+    whose layout depends on the input alone."""
     saved = {c: ks.ksort_get_tuning(c) for c in DTYPES.values()}
+    for c in DTYPES.values():
+        ks.ksort_set_tuning(c, sort_reserve=-1)
     yield
     for c, t in saved.items():
         ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
                             tile_shape=t["tile_shape"], wave_levels=t["wave_levels"],
-                            medium_tiles=t["medium_tiles"])
+                            medium_tiles=t["medium_tiles"], sort_reserve=t["sort_reserve"])
 
 
 def _dev(a):

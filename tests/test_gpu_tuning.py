@@ -27,7 +27,8 @@ def restore(ks):
     yield
     for c, t in saved.items():
         ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
-                            tile_shape=t["tile_shape"], partition_form=t["partition_form"])
+                            tile_shape=t["tile_shape"], partition_form=t["partition_form"],
+                            sort_reserve=t["sort_reserve"])
 
 
 def _sort(ks, a):
@@ -128,3 +129,19 @@ def test_autotuner_partition_kind(ks, restore, tmp_path, monkeypatch):
     t = ks.ksort_get_tuning(ks.F32)
     assert t["partition_form"] == e["tuning"]["partition_form"]
     assert t["tile_shape"] == e["tuning"]["tile_shape"]
+
+
+@pytest.mark.parametrize("reserve", [-1, 1])
+@pytest.mark.parametrize("shape", [1, 2, 3, 10])
+@pytest.mark.parametrize("dtype", list(DTYPES))
+def test_sort_offsets_by_reservation_or_lookback(ref, ks, restore, dtype, shape, reserve):
+    """Tile passes that take their output ranges by reservation (the order of tiles'
+    runs follows completion) and by look-back (tile order) both sort bit for bit as the
+    oracle does, across tile edges, presorted input and duplicate-heavy input."""
+    code = DTYPES[dtype]
+    ks.ksort_set_tuning(code, tile_shape=shape, sort_reserve=reserve)
+    assert ks.ksort_get_tuning(code)["sort_reserve"] == reserve
+    for pattern, n in (("uniform", 300_007), ("uniform", 2_000_003), ("sorted", 40_000),
+                       ("distinct16", 200_001), ("quantized15", 1_000_000)):
+        a = gen.make(pattern, dtype, n, gen.seed_for(6, 20 + shape, n % 997))
+        assert _sort(ks, a).tobytes() == _oracle(ref, a).tobytes(), (pattern, n)
