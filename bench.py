@@ -16,10 +16,13 @@ Also reported on the same line:
   exact_partition ksort_partition_exact (the paper's element order) at the same size,
                  checked byte for byte against the oracle
   batched        4096 log-uniform arrays: one graph-replayed ksort_sort_batched vs a
-                 loop of per-array ksort_sort launches
+                 loop of per-array ksort_sort launches (each arm under its own tuning,
+                 median of runs), with the batch's roofline and phase split
   serving        10,000 Poisson requests (log-uniform 1e3..1e7 keys, half float32, half
-                 uint32) served by continuous batching on a stream pool at 0.8 x the
-                 measured batched capacity: keys/s, p50/p99 latency, and every result
+                 uint32) in page-locked host memory, served by continuous batching on a
+                 stream pool, admitted into an HBM arena sized from free memory, at 0.8 x
+                 the measured capacity with copies: keys/s, p50/p99 latency from arrival
+                 (copies included), HBM budget and peak bytes in use, and every result
                  checked equal to the same request sorted alone
   clocks         SM clock and throttle reasons sampled during the timed region
 
@@ -447,7 +450,7 @@ def run_ours(args, dist: Dist):
         if "exact" in extras:
             line["exact_partition"] = run_exact_partition(ks, n, peak, peak_src)
         if "batched" in extras:
-            line["batched"] = run_batched(ks, args)
+            line["batched"] = run_batched(ks, args, peak, peak_src)
         if "serving" in extras and args.serving_requests > 0:
             bt = line.get("batched", {}).get("batched_tuning") or ks.ksort_get_tuning(ks.F32)
             line["serving"] = run_serving(ks, args.serving_requests, bt)
@@ -572,8 +575,14 @@ def run_partition_pass(ks, n, peak, peak_src, args):
         tuned = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, tile_threads=shape[0],
                      keys_per_thread=shape[1], form=shape[2], search_ms=e["ms"],
                      cached=e["cached"])
-    nt, ipt, form = ks.ksort_tile_shape(ks.F32, ks.ksort_get_tuning(ks.F32)["tile_shape"])
-    if form == 3:  # the wave form's split partition: count, then move
+    cur = ks.ksort_get_tuning(ks.F32)
+    nt, ipt, form = ks.ksort_tile_shape(ks.F32, cur["tile_shape"])
+    if cur["partition_form"] > 0:  # the ring partition (the default form)
+        pf = cur["partition_form"]
+        rnt, rtile, rocc = ks.ksort_partition_shape(ks.F32, pf)
+        kname = f"part_ring_kernel<config {pf}: {rtile}-key tiles, {rnt} threads, {rocc} CTAs/SM>"
+        launches = "one launch"
+    elif form == 3:  # the wave form's split partition: count, then move
         kname, launches = f"split_count_kernel + split_move_kernel<{nt}x{ipt}>", "two launches"
     else:
         kname, launches = f"part_kernel<{nt}x{ipt}>", "one launch"
@@ -604,7 +613,8 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     assert bool((o[:i] < o[i]).all()) and bool((o[i + 1:] >= o[i]).all())
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
                         tile_shape=saved["tile_shape"],
-                        wave_levels=saved.get("wave_levels", -1))
+                        wave_levels=saved.get("wave_levels", -1),
+                        partition_form=saved["partition_form"])
     return {"kernel": f"ksort_partition_out: {kname} <float>, {launches}",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
@@ -653,21 +663,25 @@ def run_exact_partition(ks, n, peak, peak_src):
             "method": f"{R} buffer pairs rotated, {reps} rounds, CUDA events"}
 
 
-def run_batched(ks, args):
+def run_batched(ks, args, peak, peak_src):
     """4096 arrays, lengths log-uniform in [100, 1e6]: one CUDA-graph replay of
-    ksort_sort_batched (autotuned) vs a loop of per-array ksort_sort launches (same
-    stream, the timed workload's tuning)."""
+    ksort_sort_batched (autotuned for the batch) vs a loop of per-array ksort_sort launches
+    (same stream, autotuned for the batch's mean array length). Both arms are timed the
+    same way: CUDA events around the whole batch, the median of 5 runs, the input
+    restored before each. The batch's roofline: its algorithmic bytes (2 * 4 B per key
+    each tile pass and the finisher move, from the library's counters) over the replay."""
     import torch
     from paper_1107_3622_gb300 import autotune
     sort_tuning = ks.ksort_get_tuning(ks.F32)
     lengths = gen.batched_lengths()
-    if args.no_autotune or args.tile_shape or args.cutoff:
-        tuned = {"autotuned": False}
-    else:
+    tuned = not (args.no_autotune or args.tile_shape or args.cutoff)
+    if tuned:
         e = autotune.autotune("batched", ks.F32, lengths=lengths, reps=2)
-        tuned = {"autotuned": True, "search_ms": e["ms"], "cached": e["cached"],
-                 "candidates": len(e.get("candidates", []))}
-    batched_tuning = dict(ks.ksort_get_tuning(ks.F32), **tuned)
+        info = {"autotuned": True, "search_ms": e["ms"], "cached": e["cached"],
+                "candidates": len(e.get("candidates", []))}
+    else:
+        info = {"autotuned": False}
+    batched_tuning = dict(ks.ksort_get_tuning(ks.F32), **info)
     off = gen.offsets_from_lengths(lengths)
     total = int(off[-1])
     pristine = gen.uniform_torch("f32", gen.seed_for(2, 0, 0), total, device="cuda")
@@ -680,58 +694,100 @@ def run_batched(ks, args):
         keys.copy_(pristine)
         ks.sort_batched_(keys, offs, stream=s)  # warm-up outside the graph
     torch.cuda.synchronize()
+    # one call with the library's phase events: how the batch splits
+    ks.ksort_set_phase_timing(True)
+    with torch.cuda.stream(s):
+        keys.copy_(pristine)
+        ks.sort_batched_(keys, offs, stream=s)
+    phases = ks.ksort_get_phase_times(s)
+    ks.ksort_set_phase_timing(False)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         ks.sort_batched_(keys, offs, stream=s)
-    times = []
-    for _ in range(3):
-        keys.copy_(pristine)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        g.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+
+    def timed(fn, runs=5):
+        out = []
+        for _ in range(runs):
+            keys.copy_(pristine)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out), out
+
+    t_batched, batched_runs = timed(g.replay)
     if ks.ksort_get_device_error(s):
         raise RuntimeError("device error in batched sort")
+    stats = ks.ksort_get_stats(s)
     batched_out = keys.clone()
-    t_batched = min(times)
 
-    # per-array loop, under the single-array tuning
-    ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
-                        ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
-                        tile_shape=sort_tuning["tile_shape"],
-                        wave_levels=sort_tuning.get("wave_levels", -1))
+    # per-array loop, under its own tuning: the autotuner's choice for the batch's mean
+    # array length (or the single-array tuning when autotuning is off)
+    mean_len = int(round(float(lengths.mean())))
+    if tuned:
+        ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"], tile_shape=sort_tuning["tile_shape"],
+                            wave_levels=sort_tuning.get("wave_levels", -1))
+        el = autotune.autotune("sort", ks.F32, n=mean_len, reps=3)
+        loop_info = {"autotuned": True, "for_n": mean_len, "cached": el["cached"]}
+    else:
+        ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
+                            ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
+                            tile_shape=sort_tuning["tile_shape"],
+                            wave_levels=sort_tuning.get("wave_levels", -1))
+        loop_info = {"autotuned": False}
+    loop_tuning = dict(ks.ksort_get_tuning(ks.F32), **loop_info)
     bounds = [(int(off[r]), int(off[r + 1])) for r in range(len(lengths))]
     keys.copy_(pristine)
     for b, e in bounds[:16]:
         ks.sort_(keys[b:e])
-    keys.copy_(pristine)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for b, e in bounds:
-        ks.sort_(keys[b:e])
-    e1.record()
-    torch.cuda.synchronize()
-    t_loop = e0.elapsed_time(e1)
+
+    def loop():
+        for b, e in bounds:
+            ks.sort_(keys[b:e])
+
+    t_loop, loop_runs = timed(loop, runs=3)
     if ks.ksort_get_device_error():
         raise RuntimeError("device error in per-array loop")
     same = bool(torch.equal(keys, batched_out))
+    algo = 2 * 4 * (stats["large_keys"] + stats["small_keys"])
+    gbs = algo / (t_batched / 1e3) / 1e9
+    rec = f"ksort_sort_batched<float> {tile_kernel_name(ks, ks.F32)}"
+    # restore the single-array tuning for what follows
+    ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
+                        ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
+                        tile_shape=sort_tuning["tile_shape"],
+                        wave_levels=sort_tuning.get("wave_levels", -1))
     return {"arrays": len(lengths), "total_keys": total,
             "graph_batched_ms": round(t_batched, 3),
+            "graph_batched_runs_ms": [round(x, 3) for x in batched_runs],
             "graph_batched_keys_per_s": round(total / (t_batched / 1e3), 1),
             "per_array_loop_ms": round(t_loop, 3),
+            "per_array_loop_runs_ms": [round(x, 3) for x in loop_runs],
             "per_array_loop_keys_per_s": round(total / (t_loop / 1e3), 1),
             "speedup": round(t_loop / t_batched, 2), "outputs_identical": same,
-            "batched_tuning": batched_tuning, "loop_tuning": sort_tuning}
+            "timing": "median of the runs; CUDA events around the whole batch; input restored "
+                      "before each run (untimed)",
+            "phases_ms": ({"seed": round(phases[0], 3), "partition_passes": round(phases[1], 3),
+                           "finisher": round(phases[2], 3)} if len(phases) == 3 else None),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
+                         "algorithmic_bytes_per_launch": algo,
+                         "traffic": recorded_traffic(rec, "4096-array batch, graph replay"),
+                         "kernels": "the whole graph replay: seed, wave levels or tile passes, "
+                                    "finisher"},
+            "sort_stats": stats,
+            "batched_tuning": batched_tuning, "loop_tuning": loop_tuning}
 
 
 def run_serving(ks, count: int, tuning: dict):
     """Serving configuration: `count` Poisson requests, sizes log-uniform in
-    [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys resident in HBM; the rate is
-    0.8 x the batched capacity measured on the same size mix, / mean keys per request."""
+    [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys in page-locked host memory,
+    copied into an HBM arena at admission and back when sorted; the arena is sized from
+    the HBM left free after the slot workspaces. The rate is 0.8 x the capacity measured
+    on the same size mix with the copies in line, / mean keys per request."""
     import torch
     from paper_1107_3622_gb300 import serving
     # serving batches take the batched form's tuning, for both 4-byte key types
@@ -740,32 +796,41 @@ def run_serving(ks, count: int, tuning: dict):
                             tile_shape=tuning["tile_shape"],
                             wave_levels=tuning.get("wave_levels", -1))
     cap = serving.measure_capacity()
-    rate = 0.8 * cap / serving.mean_length()
+    rate = 0.8 * cap["with_copies_keys_per_s"] / serving.mean_length()
     reqs = serving.poisson_requests(count, rate)
+    torch.cuda.empty_cache()
     t0 = time.perf_counter()
     pools = serving.build_pools(reqs)
     gen_s = time.perf_counter() - t0
     srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
     res = srv.run(reqs, pools)
     out = res.summary()
+    srv.close()
     # every result against the same request sorted alone
     t0 = time.perf_counter()
     mismatches = 0
     for r in reqs:
-        got = pools[r.dtype][r.pool_off:r.pool_off + r.n]
+        got = pools.keys(r).cuda()
         alone = serving.sort_alone(r)
         if not torch.equal(got.view(torch.int32), alone.view(torch.int32)):
             mismatches += 1
-        del alone
+        del alone, got
     if ks.ksort_get_device_error():
         raise RuntimeError("device error in the serving check")
-    out.update({"rate_per_s": round(rate, 1), "capacity_keys_per_s": round(cap, 1),
-                "slots": len(srv.slots), "slot_keys": 1 << 27,
+    out.update({"rate_per_s": round(rate, 1),
+                "capacity_keys_per_s": round(cap["with_copies_keys_per_s"], 1),
+                "capacity_sort_only_keys_per_s": round(cap["sort_keys_per_s"], 1),
+                "slots": 4, "slot_keys": 1 << 27,
+                "host_pool_bytes": pools.nbytes(),
                 "alone_vs_mix_identical": mismatches == 0, "checked": len(reqs),
                 "mismatches": mismatches, "check_s": round(time.perf_counter() - t0, 2),
                 "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning[k] for k in
                                                            ("cutoff", "ctas_per_sm", "tile_shape", "wave_levels")},
-                "latency": "arrival -> completion event of the request's batch"})
+                "latency": "arrival -> completion event of the request's batch, which follows "
+                           "the batch's host-to-device copy, sort and device-to-host copy",
+                "admission": "FIFO batches into a first-fit HBM arena sized from free memory; "
+                             "refused while the oldest request does not fit"})
+    pools.close()
     del pools
     torch.cuda.empty_cache()
     return out
@@ -787,6 +852,9 @@ def run_sweep(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     reps = 20
     rows = []
+    # the library's phase events split every timed sort into seed, partition passes and
+    # finisher (they add a few microseconds per call; the means below include them)
+    ks.ksort_set_phase_timing(True)
     for name, code, kb in (("f32", ks.F32, 4), ("f64", ks.F64, 8)):
         ks.ksort_reserve_workspace(code, max(gen.TABLE1_SIZES), 1)
         for si, n in enumerate(gen.TABLE1_SIZES):
@@ -816,6 +884,7 @@ def run_sweep(args):
                     raise RuntimeError(f"unsorted output at n={n} {name} rep {r}")
             if ks.ksort_get_device_error():
                 raise RuntimeError("device error in the sweep")
+            ph = [p for p in ks.ksort_get_phase_history(None, reps) if len(p) == 3]
             mean_ms = statistics.fmean(ms)
             gbs = statistics.fmean(algo) / (mean_ms / 1e3) / 1e9
             row = {"dtype": name, "n": n, "reps": reps, "mean_ms": round(mean_ms, 4),
@@ -825,6 +894,9 @@ def run_sweep(args):
                    # tile passes a key goes through on average (large_keys / n): the
                    # number of global partition levels, counted by the library
                    "tile_levels": round(statistics.fmean(passes), 2),
+                   "phases_ms": {k: round(statistics.fmean(p[i] for p in ph), 4)
+                                 for i, k in enumerate(("seed", "partition_passes", "finisher"))}
+                                if ph else None,
                    "paper_table1_s": PAPER_TABLE1_S[n]}
             if args.sweep_oracle_reps > 0:
                 t = []
@@ -837,6 +909,7 @@ def run_sweep(args):
                 row["oracle_reps"] = len(t)
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
+    ks.ksort_set_phase_timing(False)
     fits = {}
     for name in ("f32", "f64"):
         rs = [r for r in rows if r["dtype"] == name]

@@ -243,8 +243,10 @@ KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
  * whose tile-holding threads each hold *keys_per_thread keys (a multiple of the 128-bit
  * vector). Three CTA shapes come in four kinds (*form):
  *   0 (shapes 1-3):   every thread loads its keys of a tile straight into registers;
- *   1 (shapes 4-6):   the next tile is staged into shared memory by a bulk copy while
- *                     the current one is finished;
+ *   1 (shapes 4-6):   a ring of shared-memory tiles: one warp stages tiles by bulk
+ *                     copies, the other warps (threads - 32) compact them in place and
+ *                     take each tile's output ranges by reservation, so a CTA keeps
+ *                     several tiles in flight and no tile waits for another;
  *   2 (shapes 7-9):   warp roles, with one warp loading tiles by bulk copies, one warp
  *                     running look-backs and completions, and the rest (threads - 64)
  *                     counting, scattering and writing, so consecutive tiles overlap;
@@ -269,6 +271,14 @@ KSORT_API ksort_status_t ksort_partition_shape(ksort_dtype_t dtype, int32_t form
  * records KSORT_ERR_TIMEOUT in the stream's workspace and returns; the next
  * ksort_get_device_error(stream) reports it. No fault, trap or endless loop. */
 KSORT_API ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stream);
+
+/* Failure-path check of ksort_partition_out_noalloc: runs the same bounded wait on a
+ * look-back descriptor of the fixed device array that nothing publishes, then the
+ * call's status step, so that *key_index_dev (device int64) receives
+ * -KSORT_ERR_TIMEOUT after about limit_ms (1..60000). Allocates nothing; ordered on
+ * `stream` like any ksort_partition_out_noalloc call, whose next call starts clean. */
+KSORT_API ksort_status_t ksort_selftest_noalloc_timeout(int32_t limit_ms, int64_t *key_index_dev,
+                                                        ksort_stream_t stream);
 
 /* Diagnostics: while set, every tile pass of ksort_sort / ksort_sort_batched /
  * ksort_partition* writes 8 uint64 words per tile ticket into trace_dev[ticket * 8 ..]

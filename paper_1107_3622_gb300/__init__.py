@@ -25,11 +25,12 @@ __all__ = [
     "ksort_get_phase_history",
     "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
     "ksort_tile_keys", "ksort_tile_shape", "ksort_partition_shape", "ksort_status_string", "ksort_last_cuda_error",
-    "ksort_selftest_wait_timeout", "ksort_debug_trace",
+    "ksort_selftest_wait_timeout", "ksort_selftest_noalloc_timeout", "ksort_debug_trace",
     "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
 ]
 
 F32, F64, U32 = 0, 1, 2
+KSORT_ERR_TIMEOUT = 5
 KSORT_ERR_TOO_LARGE = 9
 KSORT_NOALLOC_MAX_KEYS = 1 << 24
 _NAMES = {F32: "f32", F64: "f64", U32: "u32"}
@@ -115,6 +116,7 @@ def load():
             "ksort_status_string": (ctypes.c_char_p, [i32]),
             "ksort_last_cuda_error": (ctypes.c_char_p, []),
             "ksort_selftest_wait_timeout": (i32, [i32, vp]),
+            "ksort_selftest_noalloc_timeout": (i32, [i32, vp, vp]),
             "ksort_debug_trace": (i32, [vp, i64]),
         }
         for name, (res, args) in sig.items():
@@ -268,7 +270,8 @@ def ksort_get_tuning(dtype: int) -> dict:
 
 def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
     """(threads, keys per tile-holding thread, form) of partition-pass form `shape`
-    (1-based); form 0 registers, 1 staged, 2 warp roles, 3 level-synchronous upper levels."""
+    (1-based); form 0 registers, 1 shared-memory tile ring, 2 warp roles, 3 level-synchronous
+    upper levels."""
     nt, ipt, fm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().ksort_tile_shape(dtype, shape, ctypes.byref(nt), ctypes.byref(ipt),
                                    ctypes.byref(fm)), "ksort_tile_shape")
@@ -294,6 +297,12 @@ def ksort_tile_keys(dtype: int) -> int:
 def ksort_selftest_wait_timeout(limit_ms: int, stream=None):
     _check(load().ksort_selftest_wait_timeout(limit_ms, _stream(stream)),
            "ksort_selftest_wait_timeout")
+
+
+def ksort_selftest_noalloc_timeout(limit_ms: int, key_index, stream=None):
+    """key_index: a device int64 tensor of one element (receives -KSORT_ERR_TIMEOUT)."""
+    _check(load().ksort_selftest_noalloc_timeout(limit_ms, _ptr(key_index), _stream(stream)),
+           "ksort_selftest_noalloc_timeout")
 
 
 def ksort_debug_trace(trace=None, tickets: int = 0):

@@ -601,11 +601,13 @@ __global__ void selftest_wait_kernel(unsigned long long *lb, Control *ctl,
 }
 
 // ------------------------------------------------------------------ fixed-scratch partition
-// ksort_partition_out_noalloc runs the same seed and tile kernels as
-// ksort_partition_out, but keeps their control block, work item, look-back descriptors
-// and ticket map in one file-scope device array instead of a per-stream workspace, so
-// that a call allocates nothing. Layout: [Control][items][item counters][small list]
-// [look-back][ticket map].
+// ksort_partition_out_noalloc makes three launches: the seed kernel, tile_kernel in its
+// default shape (variant 0) with a partition-only root, and a one-thread status kernel.
+// It keeps their control block, work item, look-back descriptors and ticket map in one
+// file-scope device array instead of a per-stream workspace, so that a call allocates
+// nothing. (ksort_partition_out's default is the ring partition, part_ring_kernel; the
+// two agree on the key index and on both sides as multisets.) Layout: [Control][items]
+// [item counters][small list][look-back][ticket map].
 constexpr unsigned long long kNoallocItems = 4;  // a single partition queues only its root
 // Tile tickets of the largest input: KSORT_NOALLOC_MAX_KEYS keys at the smallest tile
 // (4096 float64 keys), plus one for a start that is not tile-aligned, plus slack.
@@ -716,6 +718,34 @@ ksort_status_t partition_noalloc_impl(ksort_dtype_t dt, const void *in, void *ou
   KS_CUDA(ops(dt).seed(p, 0, s));
   KS_CUDA(ops(dt).tiles(p, 0, grid, s));
   noalloc_status_kernel<<<1, 1, 0, s>>>(ctl, p.key_index);
+  KS_CUDA(cudaGetLastError());
+  return KSORT_OK;
+}
+
+// Failure-path check of the fixed-scratch partition: one warp waits, as tile_kernel's
+// look-back does, for a descriptor of the fixed array that nothing publishes, gives up
+// after the limit (error word := KSORT_ERR_TIMEOUT), and the call's status kernel
+// turns the error into a negative key index.
+ksort_status_t selftest_noalloc_impl(int32_t limit_ms, int64_t *key_index, cudaStream_t s) {
+  if (limit_ms < 1 || limit_ms > 60000) return KSORT_ERR_INVALID_ARG;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  if ((st = check_device_ptr(key_index, 8, dev)) != KSORT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  NoallocDevice *d = nullptr;
+  if ((st = noalloc_device(dev, s, &d)) != KSORT_OK) return st;
+  unsigned char *b = d->base;
+  Control *ctl = reinterpret_cast<Control *>(b);
+  unsigned long long *lb = reinterpret_cast<unsigned long long *>(b + kNoallocLbOff);
+  // as at the start of a call: a clear error word; descriptor 0 at generation 0, the
+  // state of a fresh array, which the next call's seed kernel retires like any other
+  const size_t e0 = offsetof(Control, error), e1 = offsetof(Control, err_info) + 8;
+  KS_CUDA(cudaMemsetAsync(b + e0, 0, e1 - e0, s));
+  KS_CUDA(cudaMemsetAsync(&ctl->abort, 0, sizeof(unsigned), s));
+  KS_CUDA(cudaMemsetAsync(lb, 0, sizeof(unsigned long long), s));
+  selftest_wait_kernel<<<1, 32, 0, s>>>(lb, ctl, (unsigned long long)limit_ms * 1000000ull);
+  noalloc_status_kernel<<<1, 1, 0, s>>>(ctl, reinterpret_cast<long long *>(key_index));
   KS_CUDA(cudaGetLastError());
   return KSORT_OK;
 }
@@ -973,6 +1003,11 @@ ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stre
                                         (unsigned long long)limit_ms * 1000000ull);
   KS_CUDA(cudaGetLastError());
   return KSORT_OK;
+}
+
+ksort_status_t ksort_selftest_noalloc_timeout(int32_t limit_ms, int64_t *key_index_dev,
+                                              ksort_stream_t stream) {
+  return selftest_noalloc_impl(limit_ms, key_index_dev, (cudaStream_t)stream);
 }
 
 const char *ksort_status_string(ksort_status_t s) {

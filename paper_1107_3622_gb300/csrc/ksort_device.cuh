@@ -11,15 +11,17 @@
 // tile order documented at tile_kernel.
 //
 // Kernels of a sort, in stream order: seed_kernel (one CTA) starts a generation and
-// queues the roots; tile_kernel (phase 1; or its staged and warp-role forms,
-// tile_pipe_kernel and tile_ws_kernel) runs every tile pass of the sub-arrays above the
+// queues the roots; tile_kernel (phase 1; or its ring and warp-role forms,
+// tile_ring_kernel and tile_ws_kernel) runs every tile pass of the sub-arrays above the
 // cutoff, queuing sides as sub-arrays complete, until all of them are done;
 // small_kernel (phase 2) finishes the queued small sub-arrays in shared memory. The
 // wave form runs the upper levels first as wave_count_kernel / wave_scatter_kernel
 // pairs, one per level, and hands what remains to tile_kernel with wave_handoff_kernel.
-// Single partitions: part_kernel (one launch), split_count_kernel / split_move_kernel
-// (the wave form's: count, then move, no waits between CTAs), exact_*_kernel (the
-// paper's element order), and tile_kernel for the fixed-scratch entry point.
+// Single partitions: part_ring_kernel (the default, one launch; ksort_part_ring.cuh),
+// part_kernel (one launch), split_count_kernel / split_move_kernel (the wave form's:
+// count, then move, no waits between CTAs), exact_*_kernel (the paper's element order),
+// and tile_kernel for the fixed-scratch entry point. tile_ring_kernel is in
+// ksort_tile_ring.cuh.
 #pragma once
 
 #include <cstdint>
@@ -931,32 +933,33 @@ __device__ __forceinline__ void finish_item(const SortParams &p, unsigned epoch,
   const unsigned par = it.flags & kItemScratch;
   K *dst = static_cast<K *>(par ? p.keys : p.scratch);
   const K key = bits_key<K>(it.key);
+  const long long kpos = it.begin + (long long)c;
+  const bool bad = kpos >= it.end;
+  if (tid < 2) sh.ctiles[tid] = 0;
   if (tid == 0) {
-    sh.ctiles[0] = sh.ctiles[1] = 0;
-    const long long kpos = it.begin + (long long)c;
-    if (kpos >= it.end) {
+    if (bad) {
       raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)h);
     } else if (it.flags & kItemPartitionOnly) {
       dst[kpos] = key;  // a single partition: the key index is the result
       if (p.key_index) *p.key_index = (long long)c;
     } else {
       buf0[kpos] = key;  // Step 4
-      const unsigned cflags = par ^ kItemScratch;
-      const long long cb[2] = {it.begin, kpos + 1};
-      const long long ce[2] = {kpos, it.end};
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {  // Steps 5-6
-        const long long mm = ce[s] - cb[s];
-        if (mm == 1) {
-          if (cflags & kItemScratch) buf0[cb[s]] = __ldcg(dst + cb[s]);
-        } else if (mm >= 2) {
-          unsigned long long t0 = 0;
-          unsigned tiles = 0;
-          sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb[s], ce[s], cflags, &t0, &tiles);
-          sh.ct0[s] = t0;
-          sh.ctiles[s] = tiles;
-        }
-      }
+    }
+  }
+  if (tid < 2 && !bad && !(it.flags & kItemPartitionOnly)) {
+    // Steps 5-6: threads 0 and 1 queue the two sides at once (each a chain of atomics)
+    const int s = tid;
+    const unsigned cflags = par ^ kItemScratch;
+    const long long cb = s ? kpos + 1 : it.begin, ce = s ? it.end : kpos;
+    const long long mm = ce - cb;
+    if (mm == 1) {
+      if (cflags & kItemScratch) buf0[cb] = __ldcg(dst + cb);
+    } else if (mm >= 2) {
+      unsigned long long t0 = 0;
+      unsigned tiles = 0;
+      sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb, ce, cflags, &t0, &tiles);
+      sh.ct0[s] = t0;
+      sh.ctiles[s] = tiles;
     }
   }
   __syncthreads();
@@ -1350,7 +1353,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
   }
 }
 
-// Geometry of one tile pass, written by thread 0 into shared memory.
+// Geometry of one tile pass (the ring form's slots), written by the producer.
 struct PipeTile {
   Item it;
   long long h;              // item index
@@ -1359,27 +1362,6 @@ struct PipeTile {
   unsigned t;               // tile index within the item
   int vlo, vhi;             // classified keys of the tile: [vlo, vhi)
   int agg;                  // its aggregate is published already
-};
-
-// Ticket states of the staged kernel: none, claimed (not yet issued), copy in flight.
-enum : int { kPipeNone = 0, kPipeClaimed = 1, kPipeCopying = 2 };
-
-template <int NW>
-struct PipeCtaShared {
-  unsigned wl[NW], wg[NW];
-  unsigned long long E;
-  int abort;
-  int last;
-  int r;            // status of the ticket the CTA waited for
-  int cs, ns, nns;  // states of the current, next and next-but-one tiles
-  int fail;         // a warp found the next tile's keys not landed yet
-  unsigned early_L; // less keys of the next tile, counted early
-  long long ch;     // item whose record is cached in `ci`
-  Item ci;
-  PipeTile cur, nxt, nn;
-  unsigned long long cidx[2], ct0[2];
-  unsigned ctiles[2];
-  unsigned long long bar[2];
 };
 
 template <typename K, int TILE>
@@ -1414,335 +1396,8 @@ __device__ __forceinline__ void pipe_issue(const SortParams &p, const PipeTile &
   bulk_g2s(sdst, src + pt.lo, bytes, bar);
 }
 
-// Thread 0: if ticket k is issued (one acquire load of its ticket-map entry), fill `pt`
-// and start the copy of its keys into `sdst`; returns the ticket's new state.
-template <typename K, int TILE>
-__device__ __forceinline__ int pipe_try_start(const SortParams &p, unsigned epoch,
-                                              unsigned long long k, unsigned long long v,
-                                              PipeTile &pt, Item *ci, long long *ch, K *sdst,
-                                              unsigned long long *bar) {
-  pt.k = k;
-  if ((unsigned)(v >> 32) != epoch) return kPipeClaimed;
-  pipe_geom<K, TILE>(p, pt, ci, ch, k, (long long)(v & 0xffffffffull));
-  pipe_issue<K>(p, pt, sdst, bar);
-  trace_mark(p, k, 1);  // copy issued
-  return kPipeCopying;
-}
-
-__device__ __forceinline__ unsigned long long tmap_probe(const SortParams &p,
-                                                         unsigned long long k) {
-  return k < p.lb_cap ? ld_acquire(&p.tmap[k]) : 0ull;
-}
-
 template <typename K, int TILE>
 constexpr size_t pipe_smem_bytes() { return (size_t)3 * TILE * sizeof(K) + 16; }  // + copy_out_v room
-
-// Phase 1, staged form of tile_kernel: the same tile passes, Steps and output, with the
-// keys of the next tile already in shared memory when a tile starts. A CTA owns two
-// input buffers. Once a tile's output is written, its buffer is free: another thread
-// then claims the ticket after the next one and, if it is issued, starts one bulk copy of
-// its keys into that buffer, while thread 0 runs the tile's completion atomic (whose
-// release waits for the tile's stores). A copy so has a whole tile period to land. While
-// warp 0 runs a tile's look-back, the other warps count the next tile in shared memory,
-// if its keys have landed, and publish its aggregate, so later tiles' look-backs find it
-// early. A CTA holds at most two tickets beyond the finished one. A claimed ticket that
-// is not issued yet is probed again after the next tile, and waited for only when it is
-// the CTA's current tile and its previous tile is complete (that completion may be what
-// issues it). Dynamic shared memory: two input tiles and the output tile.
-template <typename K, int NT, int IPT>
-__global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_pipe_kernel(SortParams p) {
-  constexpr int TILE = NT * IPT;
-  constexpr int VEC = Vec<K>::N;
-  constexpr int NV = IPT / VEC;
-  constexpr int NW = NT / 32;
-  static_assert(IPT % VEC == 0 && IPT <= 32 && NT % 32 == 0, "bad tile shape");
-  using V = typename Vec<K>::T;
-  extern __shared__ __align__(128) unsigned char pipe_smem[];
-  K *const sin0 = reinterpret_cast<K *>(pipe_smem);
-  K *const sout = sin0 + 2 * TILE;
-  __shared__ PipeCtaShared<NW> sh;
-  K *const buf0 = static_cast<K *>(p.keys);
-  Control *ctl = p.ctl;
-  const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  unsigned long long st_tiles = 0, st_lb = 0, st_large = 0, st_large_keys = 0;
-  unsigned phase = 0;  // bit j: parity of the next completion of buffer j
-  int b = 0;           // buffer of the current tile
-
-  if (tid == 0) {
-    mbar_init(&sh.bar[0], 1);
-    mbar_init(&sh.bar[1], 1);
-    fence_mbar_init();
-    sh.ch = -1;
-    sh.cur.k = atomicAdd(&ctl->tq_head, 1ull);
-    trace_mark(p, sh.cur.k, 0);  // claimed
-    sh.cs = kPipeClaimed;
-    sh.ns = sh.nns = kPipeNone;
-    sh.fail = 0;
-    sh.early_L = 0;
-  }
-  __syncthreads();
-
-  while (true) {
-    // ---- a current tile whose ticket was not issued when claimed: wait for it now
-    if (sh.cs == kPipeClaimed) {
-      if (tid == 0) {
-        long long h = 0;
-        const int r = wait_ticket(p, epoch, sh.cur.k, &h);
-        sh.r = r;
-        if (r > 0) {
-          pipe_geom<K, TILE>(p, sh.cur, &sh.ci, &sh.ch, sh.cur.k, h);
-          pipe_issue<K>(p, sh.cur, sin0 + b * TILE, &sh.bar[b]);
-          trace_mark(p, sh.cur.k, 1);
-        }
-      }
-      __syncthreads();
-      if (sh.r <= 0) break;  // phase 1 is over (or aborted); no copy is in flight
-    }
-    K *const sin = sin0 + b * TILE;
-    K *const snx = sin0 + (b ^ 1) * TILE;
-    const bool landed = mbar_wait(&sh.bar[b], (phase >> b) & 1u, p.spin_limit_ns);
-    phase ^= 1u << b;
-
-    const int vlo = sh.cur.vlo, vhi = sh.cur.vhi;
-    const unsigned t = sh.cur.t;
-    const Item it = sh.cur.it;
-    const long long lo = sh.cur.lo, h = sh.cur.h;
-    const unsigned par = it.flags & kItemScratch;
-    K *dst = par ? buf0 : static_cast<K *>(p.scratch);
-    const K key = bits_key<K>(it.key);  // Step 1: the first element is the key
-
-    // ---- count (Step 3) from shared memory
-    K x[IPT];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const V q = *reinterpret_cast<const V *>(sin + (v * NT + tid) * VEC);
-      if constexpr (VEC == 4) {
-        x[v * 4 + 0] = q.x; x[v * 4 + 1] = q.y; x[v * 4 + 2] = q.z; x[v * 4 + 3] = q.w;
-      } else {
-        x[v * 2 + 0] = q.x; x[v * 2 + 1] = q.y;
-      }
-    }
-    unsigned lessbits = 0, gebits = 0;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-#pragma unroll
-      for (int l = 0; l < VEC; ++l) {
-        const int j = v * VEC + l, kk = (v * NT + tid) * VEC + l;
-        const bool valid = kk >= vlo && kk < vhi;
-        const bool le = goes_left(key, x[j]);
-        lessbits |= (unsigned)(valid && le) << j;
-        gebits |= (unsigned)(valid && !le) << j;
-      }
-    }
-    const unsigned mine = (unsigned)__popc(lessbits) | ((unsigned)__popc(gebits) << 16);
-    unsigned incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned u = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) {
-      sh.wl[w] = incl & 0xffffu;
-      sh.wg[w] = incl >> 16;
-    }
-    if (__syncthreads_or(!landed)) {
-      // the copy did not land in time: record it, let it finish (bounded), stop
-      if (tid == 0) raise_error(ctl, kDevTimeout, 0x800000000ull | t);
-      mbar_wait(&sh.bar[b], ((phase >> b) & 1u) ^ 1u, p.spin_limit_ns);
-      if (sh.ns == kPipeCopying) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
-      break;
-    }
-    unsigned L = 0, G = 0, wlx = 0, wgx = 0;
-#pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      const unsigned a = sh.wl[i], c = sh.wg[i];
-      if (i < w) {
-        wlx += a;
-        wgx += c;
-      }
-      L += a;
-      G += c;
-    }
-    unsigned long long *lb = p.lb + it.lb;
-    const int ns0 = sh.ns;  // state of the next tile for the rest of this iteration
-    if (tid == 0) {
-      if (!sh.cur.agg) st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));  // aggregate
-      trace_mark(p, sh.cur.k, 2);
-    }
-
-    // ---- look-back (warp 0); scatter (everyone); early count of the next tile
-    if (w == 0) {
-      unsigned long long E = 0;
-      int status = 0;
-      if (t > 0) {
-        unsigned long long steps = 0;
-        status = lookback(lb, t, epoch, p.spin_limit_ns, &ctl->abort, &E, &steps);
-        if (lane == 0) {
-          if (status == 0) st_relaxed(&lb[t], lb_pack(epoch, true, (unsigned)(E + L)));
-          st_lb += steps;
-        }
-      }
-      if (lane == 0) {
-        if (status == 1) raise_error(ctl, kDevTimeout, 0x100000000ull | t);
-        sh.E = E;
-        sh.abort = status == 0 ? 0 : 1;
-        trace_mark(p, sh.cur.k, 3);
-      }
-    }
-    scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
-    if (w > 0 && ns0 == kPipeCopying) {
-      // the next tile's copy was started a tile period ago: count it if it has landed
-      // sh.fail and sh.early_L were cleared before the CTA barrier that ended the last tile
-      const bool ok = mbar_test(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u);
-      if (__all_sync(kFull, ok)) {
-        const int nlo = sh.nxt.vlo, nhi = sh.nxt.vhi;
-        const K nkey = bits_key<K>(sh.nxt.it.key);
-        unsigned cnt = 0;
-        for (int v = tid - 32; v < TILE / VEC; v += NT - 32) {
-          const V q = *reinterpret_cast<const V *>(snx + v * VEC);
-          K y[VEC];
-          if constexpr (VEC == 4) {
-            y[0] = q.x; y[1] = q.y; y[2] = q.z; y[3] = q.w;
-          } else {
-            y[0] = q.x; y[1] = q.y;
-          }
-#pragma unroll
-          for (int l = 0; l < VEC; ++l) {
-            const int kk = v * VEC + l;
-            cnt += (kk >= nlo && kk < nhi && goes_left(nkey, y[l])) ? 1u : 0u;
-          }
-        }
-        cnt = __reduce_add_sync(kFull, cnt);
-        if (lane == 0) atomicAdd(&sh.early_L, cnt);
-      } else if (lane == 0) {
-        sh.fail = 1;
-      }
-      asm volatile("bar.sync 1, %0;" ::"r"(NT - 32) : "memory");
-      if (tid == 32 && !sh.fail) {
-        st_relaxed(&p.lb[sh.nxt.it.lb + sh.nxt.t], lb_pack(epoch, sh.nxt.t == 0, sh.early_L));
-        sh.nxt.agg = 1;
-        trace_mark(p, sh.nxt.k, 5);  // aggregate published early
-      }
-    }
-    __syncthreads();
-    const unsigned long long E = sh.E;
-    long long lbase = 0, gbase = 0;
-    const bool dest_ok = tile_dest(it.begin, it.end, lo, t, E, L, G, &lbase, &gbase);
-    if (sh.abort || !dest_ok) {
-      if (tid == 0 && !dest_ok && !sh.abort) raise_error(ctl, kDevInternal, 0x500000000ull | t);
-      if (sh.ns == kPipeCopying) mbar_wait(&sh.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_limit_ns);
-      break;
-    }
-
-    // ---- write
-    copy_out_v<K, NT>(sout, dst + lbase, L, tid);
-    copy_out_v<K, NT>(sout + L, dst + gbase, G, tid);
-    __syncthreads();
-
-    // ---- completion (thread 0), and the next copies into the buffers no longer needed
-    if (tid == 0) {
-      trace_mark(p, sh.cur.k, 4);
-      ++st_tiles;
-      if (t == it.tiles - 1 && !p.reserve) atomicExch(&p.ictl[h].less, E + L);
-      // release: this tile's writes (ordered before by the barrier) and `less` become
-      // visible to whichever CTA observes the count reaching tiles
-      const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);
-      sh.last = done_before == it.tiles - 1;
-      sh.ctiles[0] = sh.ctiles[1] = 0;
-      if (sh.last) {
-        __threadfence();
-        const unsigned long long c = ld_acquire(&p.ictl[h].less);
-        const long long kpos = it.begin + (long long)c;
-        if (kpos >= it.end) {
-          raise_error(ctl, kDevInternal, 0x700000000ull | (unsigned)h);
-        } else if (it.flags & kItemPartitionOnly) {
-          dst[kpos] = key;  // a single partition: the key index is the result
-          if (p.key_index) *p.key_index = (long long)c;
-        } else {
-          buf0[kpos] = key;  // Step 4
-          const unsigned cflags = par ^ kItemScratch;
-          const long long cb[2] = {it.begin, kpos + 1};
-          const long long ce[2] = {kpos, it.end};
-#pragma unroll
-          for (int s = 0; s < 2; ++s) {  // Steps 5-6
-            const long long mm = ce[s] - cb[s];
-            if (mm == 1) {
-              if (cflags & kItemScratch) buf0[cb[s]] = __ldcg(dst + cb[s]);
-            } else if (mm >= 2) {
-              unsigned long long t0 = 0;
-              unsigned tiles = 0;
-              sh.cidx[s] = reserve_item<K, TILE>(p, epoch, cb[s], ce[s], cflags, &t0, &tiles);
-              sh.ct0[s] = t0;
-              sh.ctiles[s] = tiles;
-            }
-          }
-        }
-      }
-      if (ns0 != kPipeCopying) {
-        // the next tile is not in flight: start it (a new claim, or the one claimed
-        // earlier), and if it starts, the one after it into this tile's buffer
-        const unsigned long long kx =
-            ns0 == kPipeClaimed ? sh.nxt.k : atomicAdd(&ctl->tq_head, 1ull);
-        if (ns0 != kPipeClaimed) trace_mark(p, kx, 0);
-        const int st = pipe_try_start<K, TILE>(p, epoch, kx, tmap_probe(p, kx), sh.nxt, &sh.ci,
-                                               &sh.ch, snx, &sh.bar[b ^ 1]);
-        sh.ns = st;
-        sh.nns = kPipeNone;
-        if (st == kPipeCopying) {
-          const unsigned long long kn = atomicAdd(&ctl->tq_head, 1ull);
-          trace_mark(p, kn, 0);
-          sh.nns = pipe_try_start<K, TILE>(p, epoch, kn, tmap_probe(p, kn), sh.nn, &sh.ci,
-                                           &sh.ch, sin, &sh.bar[b]);
-        }
-      }
-    } else if (tid == 32 && ns0 == kPipeCopying) {
-      // the next tile is in flight: the one after it goes into this tile's buffer
-      const unsigned long long kn = atomicAdd(&ctl->tq_head, 1ull);
-      trace_mark(p, kn, 0);
-      sh.nns = pipe_try_start<K, TILE>(p, epoch, kn, tmap_probe(p, kn), sh.nn, &sh.ci, &sh.ch,
-                                       sin, &sh.bar[b]);
-    }
-    __syncthreads();
-    if (sh.last) {
-#pragma unroll
-      for (int s = 0; s < 2; ++s)
-        if (sh.ctiles[s]) publish_tickets(p, epoch, sh.cidx[s], sh.ct0[s], sh.ctiles[s], tid, NT);
-      __syncthreads();
-    }
-    if (tid == 0) {
-      if (sh.last) {
-        ++st_large;
-        st_large_keys += (unsigned long long)(it.end - it.begin);
-        __threadfence();
-        atomicAdd(&ctl->large_completed, 1ull);
-      }
-      trace_mark(p, sh.cur.k, 6);  // completed
-      if (p.trace && sh.cur.k < (unsigned long long)p.trace_cap)
-        p.trace[sh.cur.k * kTraceWords + 7] = blockIdx.x;
-      // advance: the next tile becomes current
-      sh.cur = sh.nxt;
-      sh.cs = sh.ns;
-      if (sh.ns == kPipeCopying) {
-        sh.nxt = sh.nn;
-        sh.ns = sh.nns;
-      } else {
-        sh.ns = kPipeNone;
-      }
-      sh.nns = kPipeNone;
-      sh.fail = 0;
-      sh.early_L = 0;
-    }
-    __syncthreads();
-    b ^= 1;
-  }
-  if (tid == 0) {
-    if (st_tiles) atomicAdd(&ctl->tiles, st_tiles);
-    if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
-    if (st_large) atomicAdd(&ctl->large_items, st_large);
-    if (st_large_keys) atomicAdd(&ctl->large_keys, st_large_keys);
-  }
-}
 
 // ----------------------------------------------------------------------------- warp roles
 // Named barriers (0 is __syncthreads): bar.arrive / bar.sync between warp groups.

@@ -6,6 +6,7 @@
 
 #include "ksort_device.cuh"
 #include "ksort_part_ring.cuh"
+#include "ksort_tile_ring.cuh"
 
 namespace ksort {
 
@@ -26,18 +27,33 @@ template <> struct Shapes<double> {
   static constexpr int IPT[kTileShapes] = {8, 4, 8};
 };
 
-// Variant V: CTA shape V % kTileShapes in form V / kTileShapes (0 registers, 1 staged,
-// 2 warp roles, whose tile is the data warps' share: two warps load and look back; 3
-// wave levels, whose work queue then runs form 0 of the same shape).
+// Shapes of form 1 (tile_ring_kernel): data warps x keys per lane, slots, CTAs per SM,
+// tiles loading or awaiting compaction. 8-byte keys take half the keys per lane.
+template <typename K, int SH> struct RingSortOf;
+template <typename K> struct RingSortOf<K, 0> {  // 16 KiB tiles, 6 slots, 2 CTAs per SM
+  using Cfg = dev::TileRingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 3>;
+};
+template <typename K> struct RingSortOf<K, 1> {  // 8 KiB tiles, 8 slots, 3 CTAs per SM
+  using Cfg = dev::TileRingCfg<K, 8, 32 / (int)sizeof(K), 8, 3, 3>;
+};
+template <typename K> struct RingSortOf<K, 2> {  // 32 KiB tiles, 6 slots, 1 CTA per SM
+  using Cfg = dev::TileRingCfg<K, 16, 64 / (int)sizeof(K), 6, 1, 3>;
+};
+
+// Variant V: CTA shape V % kTileShapes in form V / kTileShapes (0 registers; 1 a ring of
+// shared-memory tiles, with its own three shapes; 2 warp roles, whose tile is the data
+// warps' share: two warps load and look back; 3 wave levels, whose work queue then runs
+// form 0 of the same shape).
 template <typename K, int V>
 struct ShapeOf {
   static constexpr int FORM = V / kTileShapes;
-  static constexpr int NT = Shapes<K>::NT[V % kTileShapes];
-  static constexpr int IPT = Shapes<K>::IPT[V % kTileShapes];
-  static constexpr int TILE = (FORM == 2 ? NT - 64 : NT) * IPT;
+  using Ring = typename RingSortOf<K, V % kTileShapes>::Cfg;
+  static constexpr int NT = FORM == 1 ? Ring::NT : Shapes<K>::NT[V % kTileShapes];
+  static constexpr int IPT = FORM == 1 ? Ring::IPT : Shapes<K>::IPT[V % kTileShapes];
+  static constexpr int TILE = FORM == 1 ? Ring::TILE : (FORM == 2 ? NT - 64 : NT) * IPT;
   static constexpr bool STAGED = FORM == 1 || FORM == 2;
   static constexpr size_t SMEM = FORM == 2   ? dev::ws_smem_bytes<K, TILE>()
-                                 : STAGED    ? dev::pipe_smem_bytes<K, TILE>()
+                                 : FORM == 1 ? Ring::SMEM
                                              : 0;
 };
 
@@ -64,8 +80,12 @@ decltype(auto) with_shape(int v, F &&f) {
 template <typename K, typename S>
 cudaError_t tile_kernel_of(void (**fn)(SortParams)) {
   if constexpr (S::STAGED) {
-    if constexpr (S::FORM == 2) *fn = dev::tile_ws_kernel<K, S::NT, S::IPT>;
-    else *fn = dev::tile_pipe_kernel<K, S::NT, S::IPT>;
+    if constexpr (S::FORM == 2) {
+      *fn = dev::tile_ws_kernel<K, S::NT, S::IPT>;
+    } else {
+      using R = typename S::Ring;
+      *fn = dev::tile_ring_kernel<K, R::NDW, R::IPT, R::S, R::MINB, R::DEPTH>;
+    }
     cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::SMEM);
     if (e != cudaSuccess) return e;

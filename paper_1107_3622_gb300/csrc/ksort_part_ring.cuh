@@ -99,6 +99,15 @@ struct RingStop {
     return *cta != 0 || ld_relaxed(call) == epoch;
   }
 };
+// The same for a sort: this CTA's flag, and the sort's abort flag (Control::abort, which
+// the seed kernel clears).
+struct SortStop {
+  const volatile int *cta;
+  const unsigned *call;
+  __device__ __forceinline__ bool now() const {
+    return *cta != 0 || ld_relaxed(call) != 0u;
+  }
+};
 
 // Waits, with the whole warp, for phase `parity` of `bar`: 0 once it has completed, 1
 // after limit_ns, 2 once the CTA or the call stops, 3 once ring index `i` reaches
@@ -108,8 +117,9 @@ struct RingStop {
 // phase completes or, by its definition, a system-dependent time limit passes, so the
 // checks run on every return and no wait depends on a hint being honoured. The decision
 // to leave is lane 0's, broadcast, so the warp never splits.
+template <typename Stop>
 __device__ __forceinline__ int ring_wait_warp(unsigned long long *bar, unsigned parity,
-                                              unsigned long long limit_ns, const RingStop &st,
+                                              unsigned long long limit_ns, const Stop &st,
                                               const volatile int *end_at = nullptr, int i = 0) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
@@ -131,8 +141,9 @@ __device__ __forceinline__ int ring_wait_warp(unsigned long long *bar, unsigned 
 }
 
 // The same for one thread (the producer lane).
+template <typename Stop>
 __device__ __forceinline__ int ring_wait_one(unsigned long long *bar, unsigned parity,
-                                             unsigned long long limit_ns, const RingStop &st) {
+                                             unsigned long long limit_ns, const Stop &st) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
     if (mbar_try_wait(bar, parity)) return 0;

@@ -158,3 +158,65 @@ def test_calls_leave_free_device_memory_unchanged(ks):
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
     assert int(idx.item()) == int((torch.from_numpy(a[1:]) < float(a[0])).sum())
+
+
+def test_device_error_reaches_key_index_and_next_call_is_clean(ref, ks):
+    """A device wait of the call's kind that runs past its limit on the fixed array
+    (a look-back descriptor that nothing publishes) leaves -KSORT_ERR_TIMEOUT in the key
+    index, reports nothing through ksort_get_device_error, and the next call on the same
+    stream starts clean and is right."""
+    import time
+    import torch
+    idx = torch.full((1,), -99, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ks.ksort_selftest_noalloc_timeout(100, idx)
+    torch.cuda.synchronize()
+    assert time.time() - t0 < 30
+    assert int(idx.item()) == -ks.KSORT_ERR_TIMEOUT
+    assert ks.ksort_get_device_error() == 0
+    a = gen.make("uniform", "f32", 500_003, gen.seed_for(5, 5, 0))
+    src = _dev(a)
+    got = _poisoned(src)
+    ks.ksort_partition_out_noalloc(ks.F32, src, got, a.size, idx)
+    torch.cuda.synchronize()
+    i = int(idx.item())
+    assert i == _oracle_index(ref, a)
+    want = a.copy()
+    ref.partition(want)
+    assert _same_sides(_host(got), want, i)
+
+
+def test_captured_in_a_graph_and_replayed(ref, ks):
+    """Calls captured in a CUDA graph (after a first call has done the set-up) replay
+    with no allocation; each replay partitions the inputs' current contents."""
+    import torch
+    n1, n2 = 800_001, 65_537
+    s = torch.cuda.Stream()
+    src1 = torch.empty(n1, dtype=torch.float32, device="cuda")
+    src2 = torch.empty(n2, dtype=torch.float64, device="cuda")
+    dst1, dst2 = torch.empty_like(src1), torch.empty_like(src2)
+    idx = torch.full((2,), -99, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(s):
+        ks.ksort_partition_out_noalloc(ks.F32, src1, dst1, n1, idx[0:1], stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ks.ksort_partition_out_noalloc(ks.F32, src1, dst1, n1, idx[0:1], stream=s)
+        ks.ksort_partition_out_noalloc(ks.F64, src2, dst2, n2, idx[1:2], stream=s)
+    free0, _ = torch.cuda.mem_get_info()
+    for rep in range(3):
+        a1 = gen.make("uniform", "f32", n1, gen.seed_for(5, 6, rep))
+        a2 = gen.make("uniform", "f64", n2, gen.seed_for(5, 7, rep))
+        src1.copy_(torch.from_numpy(a1))
+        src2.copy_(torch.from_numpy(a2))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        i1, i2 = idx.tolist()
+        for a, i, dst in ((a1, i1, dst1), (a2, i2, dst2)):
+            want = a.copy()
+            assert i == ref.partition(want)[0]
+            assert _same_sides(_host(dst), want, i)
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert ks.ksort_get_device_error(s) == 0
