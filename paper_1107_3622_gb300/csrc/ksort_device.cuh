@@ -697,6 +697,162 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
   return q.bad == 0;
 }
 
+// Marked form of the finisher, for sub-arrays without NaN keys (the closed form of a
+// leaf needs a total order). The partitions run as in smem_ksort, but a final segment
+// (a key at its index, a one-key side, a leaf of 2..kLeaf keys) is not finished where it
+// appears: its first index is marked in the bitmap `seg`, and in `par` when its keys are
+// in B. Bit m of `seg` closes the last segment. Once every partition is done, each
+// index of the sub-array finds its segment from the marks (a segment spans at most 32
+// indices, so the marks around it lie in at most three words), and each key goes
+// straight to its final index in `out`: a leaf key by the closed form of warp_leaf_run,
+// any other key as it stands. Warps take 32-index windows in turn, so every lane has a
+// key whatever the leaf sizes. Nothing in shared memory is written in this pass, so a
+// leaf may span windows of two warps. The result equals smem_ksort's.
+__device__ __forceinline__ void seg_mark(unsigned *bits, int i) {
+  atomicOr(&bits[i >> 5], 1u << (i & 31));
+}
+
+// A final side [cs, cs + cn) of 1..kLeaf keys, in B when cp is 1.
+__device__ __forceinline__ void mark_final(unsigned *seg, unsigned *par, int cs, int cn, int cp) {
+  if (cn < 1) return;
+  seg_mark(seg, cs);
+  if (cp) seg_mark(par, cs);
+}
+
+template <typename K>
+__device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
+                                  K *__restrict__ out, int m, SmallShared &q,
+                                  unsigned long long *segments) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int words = (m >> 5) + 2;
+  for (int i = tid; i < kSmallQueue; i += kSmallThreads) q.ring[i] = 0u;
+  for (int i = tid; i < words; i += kSmallThreads) {
+    seg[i] = 0u;
+    par[i] = 0u;
+  }
+  if (tid == 0) {
+    q.head = 0;
+    q.tail = 0;
+    q.pending = 0;
+    q.bad = 0;
+    q.nbig = 0;
+  }
+  bsync();
+  unsigned long long nseg = m <= kLeaf ? 1 : 0;
+  if (tid == 0) {
+    seg_mark(seg, m);
+    if (m <= kLeaf) mark_final(seg, par, 0, m, 0);
+    else if (m > kBlockSegment) q.big[q.nbig++] = seg_pack(0, m, 0);
+    else small_push(q, 0, m, 0);
+  }
+  bsync();
+  // CTA-wide partitions while segments are large (the top levels of the item)
+  while (q.nbig > 0) {
+    const unsigned e = q.big[q.nbig - 1];
+    const int s = (int)(e >> 16), n = (int)((e >> 1) & 0x7fffu), pe = (int)(e & 1u);
+    bsync();
+    const K *X = pe ? B : A;
+    K *Y = pe ? A : B;
+    const K key = X[s];
+    const int L = block_partition<K>(X, Y, s, n, key, q);
+    ++nseg;
+    const int cp = pe ^ 1;
+    if (tid == 0) {
+      A[s + L] = key;
+      seg_mark(seg, s + L);
+      --q.nbig;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int cs = c ? s + L + 1 : s, cn = c ? n - L - 1 : L;
+        if (cn > kBlockSegment) q.big[q.nbig++] = seg_pack(cs, cn, cp);
+        else if (cn > kLeaf) small_push(q, cs, cn, cp);
+        else mark_final(seg, par, cs, cn, cp);
+      }
+    }
+    bsync();
+  }
+  // warp-level Steps 1-6 on the queued segments (all above kLeaf keys)
+  while (true) {
+    unsigned e = 0;
+    if (lane == 0) e = small_pop(q);
+    e = __shfl_sync(kFull, e, 0);
+    if (e == 0u) break;
+    int s = (int)(e >> 16), n = (int)((e >> 1) & 0x7fffu), pe = (int)(e & 1u);
+    while (true) {
+      const K *X = pe ? B : A;
+      K *Y = pe ? A : B;
+      ++nseg;
+      const K key = X[s];  // Step 1
+      const int L = warp_partition(X, Y, s, n, key);
+      const int ls = s, ln = L, rs = s + L + 1, rn = n - L - 1, cp = pe ^ 1;
+      if (lane == 0) {
+        A[s + L] = key;  // Step 4: final index
+        seg_mark(seg, s + L);
+        if (ln <= kLeaf) mark_final(seg, par, ls, ln, cp);
+        if (rn <= kLeaf) mark_final(seg, par, rs, rn, cp);
+      }
+      // Steps 5-6: of two sides above kLeaf keys the smaller is queued and the warp
+      // keeps the other
+      const bool bl = ln > kLeaf, br = rn > kLeaf;
+      if (bl && br) {
+        if (lane == 0) {
+          if (ln < rn) small_push(q, ls, ln, cp);
+          else small_push(q, rs, rn, cp);
+        }
+        if (ln < rn) { s = rs; n = rn; } else { s = ls; n = ln; }
+        pe = cp;
+      } else if (bl) {
+        s = ls; n = ln; pe = cp;
+      } else if (br) {
+        s = rs; n = rn; pe = cp;
+      } else {
+        break;
+      }
+    }
+    if (lane == 0) {
+      __threadfence_block();
+      atomicSub(&q.pending, 1);
+    }
+  }
+  bsync();
+  // every index: its segment from the marks, its key to the final index
+  const unsigned le = lane == 31 ? kFull : ((2u << lane) - 1u);
+  const int nwin = (m + 31) >> 5;
+  bool broken = false;
+  for (int w = warp; w < nwin; w += kSmallWarps) {
+    const int i = (w << 5) + lane;
+    const unsigned cur = seg[w], nxt = seg[w + 1], prv = w > 0 ? seg[w - 1] : 0u;
+    const unsigned below = cur & le, above = cur & ~le;
+    const int s0 = below ? (w << 5) + 31 - __clz(below)
+                         : (prv ? ((w - 1) << 5) + 31 - __clz(prv) : -1);
+    const int e0 = above ? (w << 5) + __ffs(above) - 1
+                         : (nxt ? ((w + 1) << 5) + __ffs(nxt) - 1 : -1);
+    if (i >= m) continue;
+    if (s0 < 0 || e0 < 0 || e0 - s0 > kLeaf) {  // marks do not cover i: report, skip
+      broken = true;
+      continue;
+    }
+    const int n = e0 - s0, me = i - s0;
+    const K *src = ((par[s0 >> 5] >> (s0 & 31)) & 1u) ? B : A;
+    const K x = src[i];
+    int pos = me;
+    if (n >= 2) {
+      pos = 0;
+#pragma unroll 4
+      for (int j = 0; j < n; ++j) {
+        const K y = src[s0 + j];
+        // y < x (y goes left of key x), or y == x and y comes earlier
+        pos += (goes_left(x, y) || (j < me && !goes_left(y, x))) ? 1 : 0;
+      }
+    }
+    out[s0 + pos] = x;
+  }
+  if (broken) q.bad = 1;
+  bsync();
+  if (tid == 0) *segments += nseg;
+  return q.bad == 0;
+}
+
 // ----------------------------------------------------------------------------- queue
 // Work items live in a bump-allocated pool. The sort runs in two phases.
 // Phase 1 (Steps 1-4 on items above the cutoff, with Steps 5-6 queuing their sides):
@@ -2934,11 +3090,15 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) split_move_kernel(Sor
 }
 
 // Phase 2: every small sub-array, claimed from the complete list, is loaded into shared
-// memory and finished by smem_ksort. Dynamic shared memory: A and B (cutoff keys
-// each), then the per-warp leaf lists.
+// memory and finished by smem_ksort_marked, or by smem_ksort when it holds a NaN key.
+// Dynamic shared memory: A and B (cutoff keys each), the per-warp leaf lists, then the
+// two mark bitmaps (cutoff + 64 bits each).
+__host__ __device__ constexpr int small_mark_words(int cutoff) { return (cutoff >> 5) + 2; }
+
 template <typename K>
 __host__ __device__ constexpr size_t small_smem_bytes(int cutoff) {
-  return (size_t)2 * cutoff * sizeof(K) + kSmallWarps * 32 * sizeof(unsigned) + 16;
+  return (size_t)2 * cutoff * sizeof(K) + kSmallWarps * 32 * sizeof(unsigned) + 16 +
+         2 * small_mark_words(cutoff) * sizeof(unsigned);
 }
 
 struct SmallCtaShared {
@@ -2960,6 +3120,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(SortParams p) {
   K *const A = reinterpret_cast<K *>(smem);
   K *const B = A + p.cutoff;
   unsigned *const leaf_lists = reinterpret_cast<unsigned *>(B + p.cutoff);
+  unsigned *const seg = leaf_lists + kSmallWarps * 32 + 4;
+  unsigned *const par = seg + small_mark_words(p.cutoff);
   unsigned long long st_small = 0, st_small_keys = 0, st_segs = 0;
   while (true) {
     if (tid == 0) sh.r = claim_small(p, epoch, &sh.h, &sh.it);
@@ -2968,8 +3130,15 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(SortParams p) {
     const Item it = sh.it;
     const K *src = ((it.flags & kItemScratch) ? buf1 : buf0) + it.begin;
     const int m = (int)(it.end - it.begin);
-    for (int e = tid; e < m; e += kSmallThreads) A[e] = __ldcg(src + e);
-    const bool ok = smem_ksort<K>(A, B, leaf_lists, buf0 + it.begin, m, sh.q, &st_segs);
+    bool nan = false;
+    for (int e = tid; e < m; e += kSmallThreads) {
+      const K v = __ldcg(src + e);
+      A[e] = v;
+      nan |= key_is_nan(v);
+    }
+    const bool ok = __syncthreads_or(nan)
+                        ? smem_ksort<K>(A, B, leaf_lists, buf0 + it.begin, m, sh.q, &st_segs)
+                        : smem_ksort_marked<K>(A, B, seg, par, buf0 + it.begin, m, sh.q, &st_segs);
     if (tid == 0) {
       if (!ok) raise_error(ctl, kDevInternal, 0x600000000ull | (unsigned)sh.h);
       ++st_small;
