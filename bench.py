@@ -478,6 +478,29 @@ def sort_roofline(ks, stats, phases, ms_mean, n, peak, peak_src):
         gbs = bytes_ / (ms / 1e3) / 1e9 if ms > 0 else 0.0
         return round(gbs, 1), round(gbs / peak, 4)
 
+    if stats.get("launches") == 2:
+        # the fused form: one tile kernel runs the tile passes and the finisher
+        bytes_, ms = call_bytes, mean[1]
+        gbs, frac = entry(bytes_, ms)
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": frac,
+                "peak_source": f"{peak_src} hbm_gbs",
+                "traffic": recorded_traffic(rec + " fused", WORKLOAD),
+                "kernel": f"{tk} <float> with the finisher inside (finish_in_tiles): the tile "
+                          "passes of every sub-array above the cutoff and the shared-memory "
+                          "finisher of the rest (Steps 1-6)",
+                "algorithmic_bytes_per_launch": bytes_,
+                "launch_ms": round(ms, 4),
+                "timing": f"library phase events around the kernel in each of the {len(ph)} "
+                          "timed steps (ksort_set_phase_timing)",
+                "phases_ms": {"seed": round(mean[0], 4), "partition_passes": round(mean[1], 4),
+                              "finisher": round(mean[2], 4)},
+                "whole_call": {"achieved": round(call_gbs, 1), "frac": round(call_gbs / peak, 4),
+                               "algorithmic_bytes_per_call": call_bytes,
+                               "traffic": recorded_traffic(rec + " fused", WORKLOAD),
+                               "kernels": f"seed_kernel + {tk} with the finisher, one ksort_sort call"},
+                "lower_bound_bytes": 2 * 4 * n,
+                "lower_bound_frac": round((2 * 4 * n) / (ms_mean / 1e3) / 1e9 / peak, 5)}
+
     parts = {
         "partition_passes": (f"{tk} <float>: the tile passes of every sub-array above the "
                              "cutoff (Steps 1-6)", 2 * 4 * stats["large_keys"], mean[1],
@@ -614,7 +637,9 @@ def run_partition_pass(ks, n, peak, peak_src, args):
     ks.ksort_set_tuning(ks.F32, cutoff=saved["cutoff"], ctas_per_sm=saved["ctas_per_sm"] or -1,
                         tile_shape=saved["tile_shape"],
                         wave_levels=saved.get("wave_levels", -1),
-                        partition_form=saved["partition_form"])
+                        partition_form=saved["partition_form"],
+                        finish_in_tiles=saved.get("finish_in_tiles", -1),
+                        finisher_threads=saved.get("finisher_threads", 256))
     return {"kernel": f"ksort_partition_out: {kname} <float>, {launches}",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
@@ -729,14 +754,18 @@ def run_batched(ks, args, peak, peak_src):
     mean_len = int(round(float(lengths.mean())))
     if tuned:
         ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"], tile_shape=sort_tuning["tile_shape"],
-                            wave_levels=sort_tuning.get("wave_levels", -1))
+                            wave_levels=sort_tuning.get("wave_levels", -1),
+                            finish_in_tiles=sort_tuning.get("finish_in_tiles", -1),
+                            finisher_threads=sort_tuning.get("finisher_threads", 256))
         el = autotune.autotune("sort", ks.F32, n=mean_len, reps=3)
         loop_info = {"autotuned": True, "for_n": mean_len, "cached": el["cached"]}
     else:
         ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
                             ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
                             tile_shape=sort_tuning["tile_shape"],
-                            wave_levels=sort_tuning.get("wave_levels", -1))
+                            wave_levels=sort_tuning.get("wave_levels", -1),
+                            finish_in_tiles=sort_tuning.get("finish_in_tiles", -1),
+                            finisher_threads=sort_tuning.get("finisher_threads", 256))
         loop_info = {"autotuned": False}
     loop_tuning = dict(ks.ksort_get_tuning(ks.F32), **loop_info)
     bounds = [(int(off[r]), int(off[r + 1])) for r in range(len(lengths))]
@@ -759,7 +788,9 @@ def run_batched(ks, args, peak, peak_src):
     ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
                         ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
                         tile_shape=sort_tuning["tile_shape"],
-                        wave_levels=sort_tuning.get("wave_levels", -1))
+                        wave_levels=sort_tuning.get("wave_levels", -1),
+                        finish_in_tiles=sort_tuning.get("finish_in_tiles", -1),
+                            finisher_threads=sort_tuning.get("finisher_threads", 256))
     return {"arrays": len(lengths), "total_keys": total,
             "graph_batched_ms": round(t_batched, 3),
             "graph_batched_runs_ms": [round(x, 3) for x in batched_runs],
@@ -794,7 +825,9 @@ def run_serving(ks, count: int, tuning: dict):
     for code in (ks.F32, ks.U32):
         ks.ksort_set_tuning(code, cutoff=tuning["cutoff"], ctas_per_sm=tuning["ctas_per_sm"] or -1,
                             tile_shape=tuning["tile_shape"],
-                            wave_levels=tuning.get("wave_levels", -1))
+                            wave_levels=tuning.get("wave_levels", -1),
+                            finish_in_tiles=tuning.get("finish_in_tiles", -1),
+                            finisher_threads=tuning.get("finisher_threads", 256))
     cap = serving.measure_capacity()
     rate = 0.8 * cap["with_copies_keys_per_s"] / serving.mean_length()
     reqs = serving.poisson_requests(count, rate)
@@ -824,8 +857,9 @@ def run_serving(ks, count: int, tuning: dict):
                 "host_pool_bytes": pools.nbytes(),
                 "alone_vs_mix_identical": mismatches == 0, "checked": len(reqs),
                 "mismatches": mismatches, "check_s": round(time.perf_counter() - t0, 2),
-                "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning[k] for k in
-                                                           ("cutoff", "ctas_per_sm", "tile_shape", "wave_levels")},
+                "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning.get(k) for k in
+                                                           ("cutoff", "ctas_per_sm", "tile_shape", "wave_levels",
+                                                            "finish_in_tiles", "finisher_threads")},
                 "latency": "arrival -> completion event of the request's batch, which follows "
                            "the batch's host-to-device copy, sort and device-to-host copy",
                 "admission": "FIFO batches into a first-fit HBM arena sized from free memory; "

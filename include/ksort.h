@@ -220,6 +220,17 @@ KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t ma
  *                  tiles finished (the sorted result does not change; only which key heads
  *                  each later sub-array does). -1 = decoupled look-back in tile order
  *                  (the layout depends on the input alone).
+ *   finish_in_tiles: sorts in tile shape 3 only: W (1 .. 4096) = the CTAs of the tile
+ *                  passes also finish the small sub-arrays (the shared-memory finisher)
+ *                  while the tile passes run: a CTA about to take a new tile takes a
+ *                  queued small sub-array instead whenever other CTAs already wait for W
+ *                  or more tiles of sub-arrays not yet queued, and every CTA finishes the
+ *                  remaining small sub-arrays when the tile passes end, so no separate
+ *                  finisher launch follows (the finisher phase of the phase times is
+ *                  empty); -1 = off (the default): the finisher is its own launch.
+ *   finisher_threads: threads of a shared-memory finisher CTA: 256 (the default), 512
+ *                  or 1024. More threads finish one sub-array sooner (fewer CTAs fit an
+ *                  SM), which shortens sorts whose finisher is one round of sub-arrays.
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
@@ -230,6 +241,8 @@ typedef struct {
     int32_t medium_tiles;
     int32_t partition_form;
     int32_t sort_reserve;
+    int32_t finish_in_tiles;
+    int32_t finisher_threads;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);

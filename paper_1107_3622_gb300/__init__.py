@@ -64,7 +64,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("cutoff", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("spin_limit_ms", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("medium_tiles", ctypes.c_int32),
-                ("partition_form", ctypes.c_int32), ("sort_reserve", ctypes.c_int32)]
+                ("partition_form", ctypes.c_int32), ("sort_reserve", ctypes.c_int32),
+                ("finish_in_tiles", ctypes.c_int32), ("finisher_threads", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -249,13 +250,17 @@ def ksort_get_phase_times(stream=None) -> list:
 
 def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0,
                      tile_shape: int = 0, wave_levels: int = 0, medium_tiles: int = 0,
-                     partition_form: int = 0, sort_reserve: int = 0):
+                     partition_form: int = 0, sort_reserve: int = 0, finish_in_tiles: int = 0,
+                     finisher_threads: int = 0):
     """Zero arguments keep their value; ctas_per_sm=-1 restores "as many as fit",
     wave_levels=-1 the automatic level count, medium_tiles=-1 turns whole-item CTAs off,
     partition_form=-1 makes single partitions follow tile_shape instead of the ring,
-    sort_reserve=-1 makes sort tile passes take their offsets by look-back."""
+    sort_reserve=-1 makes sort tile passes take their offsets by look-back,
+    finish_in_tiles=W (tile shape 3) lets the tile kernel finish small sub-arrays while
+    W or more of its CTAs wait for future tiles; -1 gives the finisher its own launch;
+    finisher_threads (256, 512, 1024) sets the finisher CTA's size."""
     t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape, wave_levels, medium_tiles,
-               partition_form, sort_reserve)
+               partition_form, sort_reserve, finish_in_tiles, finisher_threads)
     _check(load().ksort_set_tuning(dtype, ctypes.byref(t)), "ksort_set_tuning")
 
 
@@ -265,7 +270,8 @@ def ksort_get_tuning(dtype: int) -> dict:
     return {"cutoff": t.cutoff, "ctas_per_sm": t.ctas_per_sm, "spin_limit_ms": t.spin_limit_ms,
             "tile_shape": t.tile_shape, "wave_levels": t.wave_levels,
             "medium_tiles": t.medium_tiles, "partition_form": t.partition_form,
-            "sort_reserve": t.sort_reserve}
+            "sort_reserve": t.sort_reserve, "finish_in_tiles": t.finish_in_tiles,
+            "finisher_threads": t.finisher_threads}
 
 
 def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:

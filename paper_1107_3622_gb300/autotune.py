@@ -2,14 +2,16 @@
 or a single partition), the form of the partition passes (kernel kind and threads x
 keys per thread), the number of level-synchronous levels when that form is the wave
 form, the shared-memory cutoff below which sub-arrays are finished in SMEM, and the
-finisher's CTAs per SM. For a single partition it picks the configuration of the ring
+finisher's CTAs per SM and threads per CTA, and for tile shape 3 whether the tile kernel finishes the small
+sub-arrays itself (and its park threshold). For a single partition it picks the configuration of the ring
 partition (tile size, slots, CTAs per SM), or the tile shape's own form if that wins.
 
 Every candidate runs the real workload through the C ABI on the current device. The
 input is restored from a pristine copy and L2 flushed before each timed run, and CUDA
 events time the call alone. The median over `reps` runs decides. The search is
-coordinate descent: tile shape, then wave levels (wave forms only), then cutoff, then
-finisher CTAs, repeated while something improves. The winner is checked for a sorted output, applied with
+coordinate descent: tile shape, then wave levels (wave forms only), then the fused
+finisher (tile shape 3 only), then cutoff, then finisher CTAs and their size, repeated while
+something improves. The winner is checked for a sorted output, applied with
 ksort_set_tuning, and stored in a JSON cache keyed by device, library sources, key
 type and workload, so later processes can apply it without searching.
 """
@@ -37,6 +39,10 @@ WAVE_LEVELS = (-1, 6, 9, 12, 15, 18)
 FINISHER_CTAS = (-1, 3, 2)
 # single partitions: the ring partition's configurations, or -1 (the tile shape's form)
 PARTITION_FORMS = (1, 2, 3, 4, -1)
+# tile shape 3: -1 (a separate finisher launch) or the fused finisher's park threshold
+FINISH_IN_TILES = (-1, 4, 16, 64)
+FUSED_SHAPE = 3
+FINISHER_THREADS = (256, 512, 1024)
 _L2_FLUSH_BYTES = 256 << 20
 _lock = threading.Lock()
 
@@ -104,7 +110,9 @@ def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None) -> dict | None
     t = e["tuning"]
     ksort_set_tuning(dtype, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
                      tile_shape=t["tile_shape"], wave_levels=t.get("wave_levels", -1),
-                     partition_form=t.get("partition_form", 1))
+                     partition_form=t.get("partition_form", 1),
+                     finish_in_tiles=t.get("finish_in_tiles", -1),
+                     finisher_threads=t.get("finisher_threads", 256))
     return e
 
 
@@ -198,24 +206,31 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
     best = {"tile_shape": before["tile_shape"], "cutoff": before["cutoff"],
             "ctas_per_sm": before["ctas_per_sm"] or -1,
             "wave_levels": before.get("wave_levels", -1),
-            "partition_form": before.get("partition_form", 1)}
+            "partition_form": before.get("partition_form", 1),
+            "finish_in_tiles": before.get("finish_in_tiles", -1),
+            "finisher_threads": before.get("finisher_threads", 256)}
     tried = {}
 
     def measure(cfg) -> float:
         if cfg["tile_shape"] not in WAVE_SHAPES:
             cfg["wave_levels"] = -1  # no effect outside the wave form
+        if cfg["tile_shape"] != FUSED_SHAPE:
+            cfg["finish_in_tiles"] = -1  # only tile shape 3 has the fused finisher
         key = (cfg["tile_shape"], cfg["cutoff"], cfg["ctas_per_sm"], cfg["wave_levels"],
-               cfg["partition_form"])
+               cfg["partition_form"], cfg["finish_in_tiles"], cfg["finisher_threads"])
         if key not in tried:
             ksort_set_tuning(dtype, cutoff=cfg["cutoff"], ctas_per_sm=cfg["ctas_per_sm"],
                              tile_shape=cfg["tile_shape"], wave_levels=cfg["wave_levels"],
-                             partition_form=cfg["partition_form"])
+                             partition_form=cfg["partition_form"],
+                             finish_in_tiles=cfg["finish_in_tiles"],
+                             finisher_threads=cfg["finisher_threads"])
             tried[key] = runner.time(reps)
         return tried[key]
 
     best_ms = measure(best)
-    axes = (("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS), ("cutoff", cutoffs),
-            ("ctas_per_sm", FINISHER_CTAS))
+    axes = (("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS),
+            ("finish_in_tiles", FINISH_IN_TILES), ("cutoff", cutoffs),
+            ("ctas_per_sm", FINISHER_CTAS), ("finisher_threads", FINISHER_THREADS))
     if kind == "partition":
         # the ring partition's configuration; the CTA shape only matters for the tile
         # shape's own forms (part_kernel or the split pair), under partition_form -1
@@ -224,6 +239,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
         improved = False
         for name, values in axes:
             if name == "wave_levels" and best["tile_shape"] not in WAVE_SHAPES:
+                continue
+            if name == "finish_in_tiles" and best["tile_shape"] != FUSED_SHAPE:
                 continue
             if kind == "partition" and name == "tile_shape" and best["partition_form"] != -1:
                 continue
@@ -236,17 +253,23 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
             break
     ksort_set_tuning(dtype, cutoff=best["cutoff"], ctas_per_sm=best["ctas_per_sm"],
                      tile_shape=best["tile_shape"], wave_levels=best["wave_levels"],
-                     partition_form=best["partition_form"])
+                     partition_form=best["partition_form"],
+                     finish_in_tiles=best["finish_in_tiles"],
+                     finisher_threads=best["finisher_threads"])
     if not runner.check_sorted():
         ksort_set_tuning(dtype, cutoff=before["cutoff"], ctas_per_sm=before["ctas_per_sm"] or -1,
                          tile_shape=before["tile_shape"], wave_levels=before.get("wave_levels", -1),
-                         partition_form=before.get("partition_form", 1))
+                         partition_form=before.get("partition_form", 1),
+                         finish_in_tiles=before.get("finish_in_tiles", -1),
+                         finisher_threads=before.get("finisher_threads", 256))
         raise RuntimeError("autotuned configuration produced an unsorted output")
     entry = {"workload": workload_key(kind, dtype, n, lengths), "device": device_key(),
              "library": library_hash(), "tuning": best, "ms": round(best_ms, 4),
              "keys": runner.total, "reps": reps,
              "candidates": [{"tile_shape": k[0], "cutoff": k[1], "ctas_per_sm": k[2],
-                             "wave_levels": k[3], "partition_form": k[4], "ms": round(v, 4)}
+                             "wave_levels": k[3], "partition_form": k[4],
+                             "finish_in_tiles": k[5], "finisher_threads": k[6],
+                             "ms": round(v, 4)}
                             for k, v in sorted(tried.items())]}
     if use_cache:
         _store(_full_key(kind, dtype, n, lengths), entry)
@@ -255,7 +278,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 
 def reset(dtype: int):
     """Back to the library defaults (tile shape 1, default cutoff, all finisher CTAs,
-    automatic wave levels, ring partition configuration 1)."""
+    automatic wave levels, ring partition configuration 1, separate finisher launch of
+    256-thread CTAs)."""
     default_cutoff = {F32: 4096, F64: 2048, U32: 4096}[dtype]
     ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1, wave_levels=-1,
-                     partition_form=1)
+                     partition_form=1, finish_in_tiles=-1, finisher_threads=256)

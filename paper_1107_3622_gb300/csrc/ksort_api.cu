@@ -38,7 +38,7 @@ bool dtype_ok(int dt) { return dt == KSORT_F32 || dt == KSORT_F64 || dt == KSORT
 struct Ops {
   KernelInfo (*info)(int);
   size_t (*small_smem_bytes)(int);
-  cudaError_t (*occupancy)(int, int, int *, int *);
+  cudaError_t (*occupancy)(int, int, int, int *, int *);
   cudaError_t (*seed)(const SortParams &, int, cudaStream_t);
   cudaError_t (*tiles)(const SortParams &, int, int, cudaStream_t);
   cudaError_t (*smalls)(const SortParams &, int, cudaStream_t);
@@ -54,6 +54,8 @@ struct Ops {
   RingInfo (*ring_info)(int);
   cudaError_t (*ring_occupancy)(int, int *);
   cudaError_t (*ring_partition)(const SortParams &, int, int, cudaStream_t);
+  cudaError_t (*fused_occupancy)(int, int *);
+  cudaError_t (*tiles_fused)(const SortParams &, int, cudaStream_t);
 };
 
 template <typename K>
@@ -64,7 +66,8 @@ Ops ops_for() {
              &Launcher<K>::exact_work_bytes, &Launcher<K>::exact,
              &Launcher<K>::wave_occupancy, &Launcher<K>::wave_level, &Launcher<K>::wave_handoff,
              &Launcher<K>::partition_split,
-             &Launcher<K>::ring_info,  &Launcher<K>::ring_occupancy, &Launcher<K>::ring_partition};
+             &Launcher<K>::ring_info,  &Launcher<K>::ring_occupancy, &Launcher<K>::ring_partition,
+             &Launcher<K>::fused_occupancy, &Launcher<K>::tiles_fused};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -82,13 +85,17 @@ struct Tuning {
   int medium_tiles; // register-form queue: largest item one CTA takes whole; 0: off
   int part_form;    // single partitions: ring configuration 1 .. kRingConfigs; 0: tile shape's form
   int reserve;      // sorts, register and wave forms: tile ranges by reservation (else look-back)
+  int fuse_park;    // tile variant kFusedVariant: finisher inside the tile kernel with this
+                    // park threshold; 0: separate finisher launch
+  int small_threads;  // finisher CTA: 256, 512 or 1024 threads
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1, 1}, {2048, 0, 2000, 0, 0, 0, 1, 1},
-                      {4096, 0, 2000, 0, 0, 0, 1, 1}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256},
+                      {2048, 0, 2000, 0, 0, 0, 1, 1, 0, 256},
+                      {4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -298,11 +305,12 @@ ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g)
   int sms = 0;
   ksort_status_t st = device_sms(dev, &sms);
   if (st != KSORT_OK) return st;
-  auto key = std::make_pair((int)dt * kTileVariants + tu.variant, tu.cutoff);
+  auto key = std::make_pair(((int)dt * kTileVariants + tu.variant) * 4 + tu.small_threads / 256,
+                            tu.cutoff);
   auto it = g_occ.find(key);
   std::pair<int, int> occ;
   if (it == g_occ.end()) {
-    KS_CUDA(ops(dt).occupancy(tu.variant, tu.cutoff, &occ.first, &occ.second));
+    KS_CUDA(ops(dt).occupancy(tu.variant, tu.cutoff, tu.small_threads, &occ.first, &occ.second));
     g_occ[key] = occ;
   } else {
     occ = it->second;
@@ -312,6 +320,23 @@ ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g)
   if (tu.ctas_per_sm > 0) small_occ = std::min(small_occ, tu.ctas_per_sm);
   g->tiles = sms * occ.first;
   g->smalls = sms * small_occ;
+  return KSORT_OK;
+}
+
+std::map<std::pair<int, int>, int> g_fuse_occ;  // (dtype, cutoff) -> fused tile CTAs per SM
+
+ksort_status_t fused_occupancy(ksort_dtype_t dt, int cutoff, int *occ) {
+  auto key = std::make_pair((int)dt, cutoff);
+  auto it = g_fuse_occ.find(key);
+  if (it != g_fuse_occ.end()) {
+    *occ = it->second;
+    return KSORT_OK;
+  }
+  int o = 0;
+  KS_CUDA(ops(dt).fused_occupancy(cutoff, &o));
+  if (o < 1) return KSORT_ERR_INTERNAL;
+  g_fuse_occ[key] = o;
+  *occ = o;
   return KSORT_OK;
 }
 
@@ -389,6 +414,7 @@ SortParams sort_params(const Workspace &ws, void *keys, const Tuning &tu) {
   p.lb = ws.lb;
   p.lb_cap = ws.lb_cap;
   p.cutoff = tu.cutoff;
+  p.small_threads = tu.small_threads;
   p.spin_limit_ns = (unsigned long long)tu.spin_limit_ms * 1000000ull;
   p.trace = g_trace;
   p.trace_cap = g_trace_cap;
@@ -578,6 +604,31 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     ws->launches = 2ull * (unsigned long long)levels + 4ull;
     return KSORT_OK;
   }
+  if (tu.fuse_park > 0 && tu.variant == kFusedVariant && (offsets || total > tu.cutoff)) {
+    // the tile kernel finishes the small items too: while enough of its CTAs already
+    // wait for tiles of items still to come, the others take small items, and all of
+    // them drain the small list at the end; no finisher launch follows
+    int focc = 0, sms = 0;
+    if ((st = fused_occupancy(dt, tu.cutoff, &focc)) != KSORT_OK) return st;
+    if ((st = device_sms(dev, &sms)) != KSORT_OK) return st;
+    long long grid = (long long)sms * focc;
+    if (!offsets) {
+      const long long first = (total + kinfo.tile_keys - 1) / kinfo.tile_keys;
+      const long long smalls = 2 * ((total + tu.cutoff - 1) / tu.cutoff);
+      grid = std::max<long long>(1, std::min<long long>(grid, std::max(first, smalls)));
+    }
+    p.fuse_park = tu.fuse_park;
+    PhaseMarks pm;
+    if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
+    KS_CUDA(pm.mark());
+    KS_CUDA(ops(dt).seed(p, tu.variant, s));
+    KS_CUDA(pm.mark());
+    KS_CUDA(ops(dt).tiles_fused(p, (int)grid, s));
+    KS_CUDA(pm.mark());
+    KS_CUDA(pm.mark());  // the finisher phase is empty: its work ran inside the tile kernel
+    ws->launches = 2;
+    return KSORT_OK;
+  }
   PhaseMarks pm;
   if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
   KS_CUDA(pm.mark());
@@ -641,7 +692,8 @@ ksort_status_t noalloc_device(int dev, cudaStream_t s, NoallocDevice **out) {
     KS_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     for (int t = 0; t < 3; ++t) {
       int small_ctas = 0;
-      KS_CUDA(ops((ksort_dtype_t)t).occupancy(0, g_tuning[t].cutoff, &d.tile_ctas[t], &small_ctas));
+      KS_CUDA(ops((ksort_dtype_t)t).occupancy(0, g_tuning[t].cutoff, 256, &d.tile_ctas[t],
+                                              &small_ctas));
       if (d.tile_ctas[t] < 1) return KSORT_ERR_INTERNAL;
     }
     KS_CUDA(cudaMemsetAsync(base, 0, kNoallocBytes, s));
@@ -948,6 +1000,10 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->medium_tiles < -1 || t->medium_tiles > kMediumMaxTiles) return KSORT_ERR_INVALID_ARG;
   if (t->partition_form < -1 || t->partition_form > kRingConfigs) return KSORT_ERR_INVALID_ARG;
   if (t->sort_reserve < -1 || t->sort_reserve > 1) return KSORT_ERR_INVALID_ARG;
+  if (t->finish_in_tiles < -1 || t->finish_in_tiles > 4096) return KSORT_ERR_INVALID_ARG;
+  if (t->finisher_threads != 0 && t->finisher_threads != 256 && t->finisher_threads != 512 &&
+      t->finisher_threads != 1024)
+    return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
@@ -958,6 +1014,8 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->medium_tiles) g.medium_tiles = t->medium_tiles < 0 ? 0 : t->medium_tiles;
   if (t->partition_form) g.part_form = t->partition_form < 0 ? 0 : t->partition_form;
   if (t->sort_reserve) g.reserve = t->sort_reserve > 0 ? 1 : 0;
+  if (t->finish_in_tiles) g.fuse_park = t->finish_in_tiles < 0 ? 0 : t->finish_in_tiles;
+  if (t->finisher_threads) g.small_threads = t->finisher_threads;
   return KSORT_OK;
 }
 
@@ -974,6 +1032,8 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->medium_tiles = g.medium_tiles ? g.medium_tiles : -1;
   out->partition_form = g.part_form ? g.part_form : -1;
   out->sort_reserve = g.reserve ? 1 : -1;
+  out->finish_in_tiles = g.fuse_park ? g.fuse_park : -1;
+  out->finisher_threads = g.small_threads;
   return KSORT_OK;
 }
 

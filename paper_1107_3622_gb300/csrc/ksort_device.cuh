@@ -32,8 +32,7 @@ namespace ksort {
 namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSmallThreads = 256;  // small_kernel CTA
-constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kSmallThreads = 256;  // default small_kernel CTA (512 and 1024 also built)
 
 #ifndef KSORT_LOOKBACK_PER
 #define KSORT_LOOKBACK_PER 1
@@ -338,7 +337,7 @@ __device__ __forceinline__ bool tile_dest(long long begin, long long end, long l
 
 // ----------------------------------------------------------------------------- smem
 // Shared-memory finisher for one small sub-array (m <= cutoff keys) staged in buffer A,
-// run by one CTA of kSmallThreads threads. Its warps apply Steps 1-6: first CTA-wide partitions
+// run by one CTA of 256, 512 or 1024 threads. Its warps apply Steps 1-6: first CTA-wide partitions
 // while a segment is larger than kBlockSegment keys, then one warp per segment (Steps
 // 1-4 by ballots from one buffer into the other; Steps 5-6 depth first, the smaller
 // side queued for another warp), and sides of at most kLeaf keys become leaves that
@@ -484,10 +483,10 @@ __device__ __forceinline__ unsigned small_pop(SmallShared &q) {
 // Steps 1-4 by all warps of the CTA on X[s .. s+n): each warp classifies a contiguous
 // run of 32-key chunks twice (count, then scatter after a scan of the warp counts). Same
 // layout as warp_partition. Returns L; contains three CTA barriers.
-template <typename K>
+template <typename K, int NT>
 __device__ __forceinline__ int block_partition(const K *X, K *Y, int s, int n, K key,
                                                SmallShared &q) {
-  constexpr int NW = kSmallWarps;
+  constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
   const int e = s + n;
@@ -571,13 +570,14 @@ __device__ __forceinline__ int warp_partition(const K *X, K *Y, int s, int n, K 
 }
 
 // Sorts A[0..m) (staged keys) with the K-sort rule into out[0..m); B is scratch of at
-// least m keys. Run by the whole CTA; returns false if a consistency check failed.
-template <typename K>
+// least m keys. Run by the whole CTA of NT threads; returns false if a consistency
+// check failed.
+template <typename K, int NT>
 __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out, int m,
                            SmallShared &q, unsigned long long *segments) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned *leaves = leaf_lists + warp * 32;
-  for (int i = tid; i < kSmallQueue; i += kSmallThreads) q.ring[i] = 0u;
+  for (int i = tid; i < kSmallQueue; i += NT) q.ring[i] = 0u;
   if (tid == 0) {
     q.head = 0;
     q.tail = 0;
@@ -608,7 +608,7 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
       const K *X = par ? B : A;
       K *Y = par ? A : B;
       const K key = X[s];
-      const int L = block_partition<K>(X, Y, s, n, key, q);
+      const int L = block_partition<K, NT>(X, Y, s, n, key, q);
       ++nseg;
       const int cp = par ^ 1;
       if (tid == 0) {
@@ -692,7 +692,7 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
     if (nleaves) warp_leaf_run(A, B, leaves, nleaves, nlanes);
   }
   bsync();
-  copy_out_v<K, kSmallThreads>(A, out, (unsigned)m, tid);
+  copy_out_v<K, NT>(A, out, (unsigned)m, tid);
   if (tid == 0) *segments += nseg;
   return q.bad == 0;
 }
@@ -719,14 +719,14 @@ __device__ __forceinline__ void mark_final(unsigned *seg, unsigned *par, int cs,
   if (cp) seg_mark(par, cs);
 }
 
-template <typename K>
+template <typename K, int NT>
 __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
                                   K *__restrict__ out, int m, SmallShared &q,
                                   unsigned long long *segments) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int words = (m >> 5) + 2;
-  for (int i = tid; i < kSmallQueue; i += kSmallThreads) q.ring[i] = 0u;
-  for (int i = tid; i < words; i += kSmallThreads) {
+  for (int i = tid; i < kSmallQueue; i += NT) q.ring[i] = 0u;
+  for (int i = tid; i < words; i += NT) {
     seg[i] = 0u;
     par[i] = 0u;
   }
@@ -754,7 +754,7 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
     const K *X = pe ? B : A;
     K *Y = pe ? A : B;
     const K key = X[s];
-    const int L = block_partition<K>(X, Y, s, n, key, q);
+    const int L = block_partition<K, NT>(X, Y, s, n, key, q);
     ++nseg;
     const int cp = pe ^ 1;
     if (tid == 0) {
@@ -819,7 +819,7 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
   const unsigned le = lane == 31 ? kFull : ((2u << lane) - 1u);
   const int nwin = (m + 31) >> 5;
   bool broken = false;
-  for (int w = warp; w < nwin; w += kSmallWarps) {
+  for (int w = warp; w < nwin; w += NT / 32) {
     const int i = (w << 5) + lane;
     const unsigned cur = seg[w], nxt = seg[w + 1], prv = w > 0 ? seg[w - 1] : 0u;
     const unsigned below = cur & le, above = cur & ~le;
@@ -852,6 +852,29 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
   if (tid == 0) *segments += nseg;
   return q.bad == 0;
 }
+
+// Dynamic shared memory of a finisher CTA of nt threads: A and B (cutoff keys each),
+// the per-warp leaf lists, then the two mark bitmaps (cutoff + 64 bits each).
+__host__ __device__ constexpr int small_mark_words(int cutoff) { return (cutoff >> 5) + 2; }
+template <typename K>
+__host__ __device__ constexpr size_t small_smem_bytes(int cutoff, int nt = kSmallThreads) {
+  return (size_t)2 * cutoff * sizeof(K) + (size_t)nt * sizeof(unsigned) + 16 +
+         2 * small_mark_words(cutoff) * sizeof(unsigned);
+}
+
+// The finisher's shared memory carved from one dynamic allocation (at `base`).
+template <typename K>
+struct SmallSmem {
+  K *A, *B;
+  unsigned *leaf_lists, *seg, *par;
+  __device__ SmallSmem(unsigned char *base, int cutoff, int nt) {
+    A = reinterpret_cast<K *>(base);
+    B = A + cutoff;
+    leaf_lists = reinterpret_cast<unsigned *>(B + cutoff);
+    seg = leaf_lists + nt + 4;
+    par = seg + small_mark_words(cutoff);
+  }
+};
 
 // ----------------------------------------------------------------------------- queue
 // Work items live in a bump-allocated pool. The sort runs in two phases.
@@ -888,15 +911,14 @@ __device__ __forceinline__ unsigned long long reserve_item(const SortParams &p, 
   // a medium item takes one ticket; its CTA runs all of its tile passes
   const bool medium = !small && tiles >= 2 && (int)tiles <= p.medium_tiles;
   const unsigned tickets = medium ? 1u : tiles;
-  unsigned long long t0 = 0;
-  if (!small) {
-    t0 = atomicAdd(&ctl->lb_used, (unsigned long long)tickets);
-    if (t0 + tickets > p.lb_cap) {
-      raise_error(ctl, kDevWorkspaceExhausted, 2);
-      return 0;
-    }
-  }
+  // the key load and both atomics are independent: all three are in flight at once
+  const K first = __ldcg(buf + b);
+  const unsigned long long t0 = small ? 0ull : atomicAdd(&ctl->lb_used, (unsigned long long)tickets);
   const unsigned long long idx = atomicAdd(&ctl->pushed, 1ull);
+  if (!small && t0 + tickets > p.lb_cap) {
+    raise_error(ctl, kDevWorkspaceExhausted, 2);
+    return 0;
+  }
   if (idx >= p.item_cap) {
     raise_error(ctl, kDevWorkspaceExhausted, 1);
     return 0;
@@ -904,7 +926,7 @@ __device__ __forceinline__ unsigned long long reserve_item(const SortParams &p, 
   Item *it = p.items + idx;
   it->begin = b;
   it->end = e;
-  it->key = key_bits<K>(__ldcg(buf + b));
+  it->key = key_bits<K>(first);
   it->tiles = tiles;
   it->lb = (unsigned)t0;
   it->flags = flags | (small ? kItemSmall : 0u) | (medium ? kItemMedium : 0u);
@@ -999,6 +1021,73 @@ __device__ __forceinline__ int claim_small(const SortParams &p, unsigned epoch, 
       if (t0 == 0) t0 = now;
       if (now - t0 > p.spin_limit_ns) {
         raise_error(ctl, kDevTimeout, 0x200000000ull | j);
+        return -1;
+      }
+    }
+    __nanosleep(32);
+  }
+}
+
+// A CTA of NT threads, any phase: the small item `it` (index h) is loaded into shared
+// memory and finished there by smem_ksort_marked, or by smem_ksort when it holds a NaN
+// key; its keys end in buffer 0. Ends with a CTA barrier.
+template <typename K, int NT>
+__device__ __forceinline__ void finish_small_item(const SortParams &p, const Item &it, long long h,
+                                                  K *buf0, const K *buf1, const SmallSmem<K> &sm,
+                                                  SmallShared &q, unsigned long long *st_small,
+                                                  unsigned long long *st_small_keys,
+                                                  unsigned long long *st_segs) {
+  const int tid = threadIdx.x;
+  const K *src = ((it.flags & kItemScratch) ? buf1 : buf0) + it.begin;
+  const int m = (int)(it.end - it.begin);
+  bool nan = false;
+  for (int e = tid; e < m; e += NT) {
+    const K v = __ldcg(src + e);
+    sm.A[e] = v;
+    nan |= key_is_nan(v);
+  }
+  const bool ok = __syncthreads_or(nan)
+                      ? smem_ksort<K, NT>(sm.A, sm.B, sm.leaf_lists, buf0 + it.begin, m, q,
+                                          st_segs)
+                      : smem_ksort_marked<K, NT>(sm.A, sm.B, sm.seg, sm.par, buf0 + it.begin, m,
+                                                 q, st_segs);
+  if (tid == 0) {
+    if (!ok) raise_error(p.ctl, kDevInternal, 0x600000000ull | (unsigned)h);
+    ++*st_small;
+    *st_small_keys += (unsigned long long)m;
+  }
+  __syncthreads();
+}
+
+// One thread, phase 1: claims the next small item only if one is queued now (the list
+// is still growing, so the head moves by compare-and-swap and never passes the tail).
+// Returns 1 with the item, 0 when none is queued, -1 on abort or timeout.
+__device__ __forceinline__ int try_claim_small(const SortParams &p, unsigned epoch,
+                                               long long *h_out, Item *it_out) {
+  Control *ctl = p.ctl;
+  if (ld_relaxed(&ctl->abort)) return -1;
+  unsigned long long j = ld_relaxed(&ctl->sq_head);
+  while (true) {
+    const unsigned long long tail = ld_acquire(&ctl->sq_tail);
+    if (j >= tail || j >= p.item_cap) return 0;
+    const unsigned long long prev = atomicCAS(&ctl->sq_head, j, j + 1);
+    if (prev == j) break;
+    j = prev;
+  }
+  unsigned long long t0 = 0;
+  for (unsigned spins = 1;; ++spins) {  // its pusher has taken the slot: the entry follows
+    const unsigned long long v = ld_acquire(&p.small_q[j]);
+    if ((unsigned)(v >> 32) == epoch) {
+      const long long idx = (long long)(v & 0xffffffffull);
+      load_item(p.items + idx, it_out);
+      *h_out = idx;
+      return 1;
+    }
+    if ((spins & 255u) == 0u) {
+      const unsigned long long now = globaltimer();
+      if (t0 == 0) t0 = now;
+      if (now - t0 > p.spin_limit_ns) {
+        raise_error(ctl, kDevTimeout, 0xC00000000ull | j);
         return -1;
       }
     }
@@ -1131,7 +1220,13 @@ __device__ __forceinline__ void finish_item(const SortParams &p, unsigned epoch,
   }
 }
 
-template <typename K, int NT, int IPT>
+// FUSE: the CTAs also finish small items (dynamic shared memory: SmallShared, then the
+// finisher's buffers for p.cutoff keys). A CTA about to
+// claim a ticket takes a queued small item instead while at least p.fuse_park tickets
+// are held beyond the ones issued (CTAs already parked for items still to come), and
+// every CTA drains the small list once the tile passes are over, so no finisher launch
+// follows.
+template <typename K, int NT, int IPT, bool FUSE>
 __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParams p) {
   constexpr int TILE = NT * IPT;
   constexpr int VEC = Vec<K>::N;
@@ -1150,12 +1245,28 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
   unsigned long long st_tiles = 0, st_lb = 0, st_large = 0, st_large_keys = 0;
   long long cached_h = -1;
   unsigned long long k_next = ~0ull;  // ticket claimed at the end of the previous tile
+  extern __shared__ __align__(16) unsigned char fuse_smem[];
+  unsigned long long st_small = 0, st_small_keys = 0, st_segs = 0;
 
   while (true) {
     // ---- claim: tickets are taken only when the CTA is about to load them, so
     // consecutive tickets are worked on at about the same time and look-backs find
     // their predecessors' aggregates already published
-    if (tid == 0) {
+    int fr = 0;
+    if constexpr (FUSE) {
+      if (tid == 0 && k_next == ~0ull) {
+        const unsigned long long head = ld_relaxed(&ctl->tq_head);
+        const unsigned long long used = ld_relaxed(&ctl->lb_used);
+        if (head >= used + (unsigned long long)p.fuse_park) {
+          fr = try_claim_small(p, epoch, &sh.h, &sh.it);
+          if (fr != 0) {
+            sh.r = fr > 0 ? 2 : -1;
+            cached_h = -1;
+          }
+        }
+      }
+    }
+    if (tid == 0 && fr == 0) {
       const unsigned long long k = k_next != ~0ull ? k_next : atomicAdd(&ctl->tq_head, 1ull);
       k_next = ~0ull;
       long long h = 0;
@@ -1186,6 +1297,25 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       }
     }
     __syncthreads();
+    if constexpr (FUSE) {
+      SmallShared &q = *reinterpret_cast<SmallShared *>(fuse_smem);
+      const SmallSmem<K> sm(fuse_smem + (sizeof(SmallShared) + 15) / 16 * 16, p.cutoff, NT);
+      if (sh.r == 2) {  // a small item, taken while other CTAs wait for tiles
+        finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, q, &st_small, &st_small_keys,
+                                 &st_segs);
+        continue;
+      }
+      if (sh.r == 0) {  // the tile passes are over: drain the small list
+        while (true) {
+          if (tid == 0) sh.r = claim_small(p, epoch, &sh.h, &sh.it);
+          __syncthreads();
+          if (sh.r <= 0) break;
+          finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, q, &st_small,
+                                   &st_small_keys, &st_segs);
+        }
+        break;
+      }
+    }
     if (sh.r <= 0) break;
     if (sh.it.flags & kItemMedium) {
       // ---- a medium item: this CTA runs all its tile passes, counting first and then
@@ -1288,7 +1418,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       }
       if (bad) break;
       if (tid == 0) {
-        k_next = atomicAdd(&ctl->tq_head, 1ull);
+        if (!FUSE) k_next = atomicAdd(&ctl->tq_head, 1ull);
         st_tiles += T;
       }
       finish_item<K, TILE, NW>(p, epoch, it, h, E, sh, st_large, st_large_keys);
@@ -1428,7 +1558,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       // release: this tile's writes (ordered before by the barrier) and `less` become
       // visible to whichever CTA observes the count reaching tiles
       const unsigned done_before = atom_add_release(&p.ictl[h].done, 1u);
-      k_next = atomicAdd(&ctl->tq_head, 1ull);  // the next ticket (its claim overlaps)
+      if (!FUSE) k_next = atomicAdd(&ctl->tq_head, 1ull);  // the next ticket (its claim overlaps)
       sh.last = done_before == it.tiles - 1;
       if (sh.last) {
         __threadfence();
@@ -1445,7 +1575,16 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
     if (st_lb) atomicAdd(&ctl->lookback_steps, st_lb);
     if (st_large) atomicAdd(&ctl->large_items, st_large);
     if (st_large_keys) atomicAdd(&ctl->large_keys, st_large_keys);
+    if (st_small) atomicAdd(&ctl->small_items, st_small);
+    if (st_small_keys) atomicAdd(&ctl->small_keys, st_small_keys);
+    if (st_segs) atomicAdd(&ctl->smem_levels, st_segs);
   }
+}
+
+// Dynamic shared memory of the fused tile kernel.
+template <typename K>
+__host__ __device__ constexpr size_t fuse_smem_bytes(int cutoff, int nt) {
+  return (sizeof(SmallShared) + 15) / 16 * 16 + small_smem_bytes<K>(cutoff, nt);
 }
 
 // ----------------------------------------------------------------------------- staged
@@ -3089,17 +3228,8 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) split_move_kernel(Sor
     raise_error(p.ctl, kDevInternal, 0xA00000000ull | 0xFFFFFFFFull);
 }
 
-// Phase 2: every small sub-array, claimed from the complete list, is loaded into shared
-// memory and finished by smem_ksort_marked, or by smem_ksort when it holds a NaN key.
-// Dynamic shared memory: A and B (cutoff keys each), the per-warp leaf lists, then the
-// two mark bitmaps (cutoff + 64 bits each).
-__host__ __device__ constexpr int small_mark_words(int cutoff) { return (cutoff >> 5) + 2; }
-
-template <typename K>
-__host__ __device__ constexpr size_t small_smem_bytes(int cutoff) {
-  return (size_t)2 * cutoff * sizeof(K) + kSmallWarps * 32 * sizeof(unsigned) + 16 +
-         2 * small_mark_words(cutoff) * sizeof(unsigned);
-}
+// Phase 2: every small sub-array, claimed from the complete list, is finished by
+// finish_small_item.
 
 struct SmallCtaShared {
   SmallShared q;
@@ -3108,8 +3238,8 @@ struct SmallCtaShared {
   Item it;
 };
 
-template <typename K>
-__global__ void __launch_bounds__(kSmallThreads) small_kernel(SortParams p) {
+template <typename K, int NT>
+__global__ void __launch_bounds__(NT) small_kernel(SortParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ SmallCtaShared sh;
   K *const buf0 = static_cast<K *>(p.keys);
@@ -3117,34 +3247,14 @@ __global__ void __launch_bounds__(kSmallThreads) small_kernel(SortParams p) {
   Control *ctl = p.ctl;
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const int tid = threadIdx.x;
-  K *const A = reinterpret_cast<K *>(smem);
-  K *const B = A + p.cutoff;
-  unsigned *const leaf_lists = reinterpret_cast<unsigned *>(B + p.cutoff);
-  unsigned *const seg = leaf_lists + kSmallWarps * 32 + 4;
-  unsigned *const par = seg + small_mark_words(p.cutoff);
+  const SmallSmem<K> sm(smem, p.cutoff, NT);
   unsigned long long st_small = 0, st_small_keys = 0, st_segs = 0;
   while (true) {
     if (tid == 0) sh.r = claim_small(p, epoch, &sh.h, &sh.it);
     __syncthreads();
     if (sh.r <= 0) break;
-    const Item it = sh.it;
-    const K *src = ((it.flags & kItemScratch) ? buf1 : buf0) + it.begin;
-    const int m = (int)(it.end - it.begin);
-    bool nan = false;
-    for (int e = tid; e < m; e += kSmallThreads) {
-      const K v = __ldcg(src + e);
-      A[e] = v;
-      nan |= key_is_nan(v);
-    }
-    const bool ok = __syncthreads_or(nan)
-                        ? smem_ksort<K>(A, B, leaf_lists, buf0 + it.begin, m, sh.q, &st_segs)
-                        : smem_ksort_marked<K>(A, B, seg, par, buf0 + it.begin, m, sh.q, &st_segs);
-    if (tid == 0) {
-      if (!ok) raise_error(ctl, kDevInternal, 0x600000000ull | (unsigned)sh.h);
-      ++st_small;
-      st_small_keys += (unsigned long long)m;
-    }
-    __syncthreads();
+    finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, sh.q, &st_small, &st_small_keys,
+                             &st_segs);
   }
   if (tid == 0) {
     if (st_small) atomicAdd(&ctl->small_items, st_small);

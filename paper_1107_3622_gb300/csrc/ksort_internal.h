@@ -126,6 +126,9 @@ struct SortParams {
   int wave;                  // nonzero: the seed queues large roots on the level-0 list
   int medium_tiles;          // items of 2 .. medium_tiles tile passes go to one CTA; 0: off
   int reserve;               // tile_kernel: output ranges by reservation, not look-back
+  int small_threads;         // small_kernel CTA: 256, 512 or 1024 threads
+  int fuse_park;             // fused tile_kernel: tickets held ahead of the issued ones
+                             // before a CTA takes a small item instead of a ticket
 };
 constexpr int kTraceWords = 8;
 
@@ -140,6 +143,10 @@ constexpr int kTileForms = 4;
 constexpr int kWaveForm = 3;
 constexpr int kWaveMaxGrid = 4096;  // CTAs of one level pass (two counts each)
 constexpr int kTileVariants = kTileForms * kTileShapes;
+// The tile variant whose CTAs can also finish small items (queue form, 256 threads).
+constexpr int kFusedVariant = 2;
+// Threads of a finisher CTA: 256 (the default), 512 or 1024.
+constexpr int small_threads_of(int nt) { return nt == 1024 || nt == 512 ? nt : 256; }
 
 struct KernelInfo {
   int block;          // threads per tile-pass CTA
@@ -163,10 +170,14 @@ template <typename K>
 struct Launcher {
   static KernelInfo info(int variant);
   static size_t small_smem_bytes(int cutoff);
-  static cudaError_t occupancy(int variant, int cutoff, int *tile_ctas, int *small_ctas);
+  // CTAs per SM of the tile kernel of `variant` and of the finisher of nt threads
+  static cudaError_t occupancy(int variant, int cutoff, int nt, int *tile_ctas, int *small_ctas);
   static cudaError_t seed(const SortParams &p, int variant, cudaStream_t s);
   static cudaError_t tiles(const SortParams &p, int variant, int grid, cudaStream_t s);
   static cudaError_t smalls(const SortParams &p, int grid, cudaStream_t s);
+  // tile_kernel in tile variant kFusedVariant with the finisher inside (no smalls launch)
+  static cudaError_t fused_occupancy(int cutoff, int *ctas);
+  static cudaError_t tiles_fused(const SortParams &p, int grid, cudaStream_t s);
   static long long tile_count(int variant, const void *buf, long long begin, long long end);
   // single partitions: part_kernel with CTA shape `shape` (0 .. kTileShapes - 1)
   static cudaError_t part_occupancy(int shape, int *ctas);

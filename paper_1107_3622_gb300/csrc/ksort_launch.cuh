@@ -92,7 +92,7 @@ cudaError_t tile_kernel_of(void (**fn)(SortParams)) {
     return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared);
   } else {
-    *fn = dev::tile_kernel<K, S::NT, S::IPT>;
+    *fn = dev::tile_kernel<K, S::NT, S::IPT, false>;
     return cudaSuccess;
   }
 }
@@ -101,8 +101,19 @@ cudaError_t tile_kernel_of(void (**fn)(SortParams)) {
 // CTA's shared memory (227 KB), so 8-byte keys stop at half the 4-byte limit.
 template <typename K>
 constexpr int max_cutoff() { return sizeof(K) == 8 ? dev::kMaxSmallCutoff / 2 : dev::kMaxSmallCutoff; }
-static_assert(dev::small_smem_bytes<double>(max_cutoff<double>()) <= 227 * 1024, "smem");
-static_assert(dev::small_smem_bytes<float>(max_cutoff<float>()) <= 227 * 1024, "smem");
+static_assert(dev::small_smem_bytes<double>(max_cutoff<double>(), 1024) <= 227 * 1024, "smem");
+static_assert(dev::small_smem_bytes<float>(max_cutoff<float>(), 1024) <= 227 * 1024, "smem");
+
+// The finisher kernel of nt threads (256, 512 or 1024; anything else: 256), with its
+// dynamic shared memory for `cutoff`-key items allowed.
+template <typename K>
+cudaError_t small_kernel_of(int nt, int cutoff, void (**fn)(SortParams), size_t *smem) {
+  *fn = nt == 1024 ? dev::small_kernel<K, 1024>
+      : nt == 512  ? dev::small_kernel<K, 512>
+                   : dev::small_kernel<K, dev::kSmallThreads>;
+  *smem = dev::small_smem_bytes<K>(cutoff, small_threads_of(nt));
+  return cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+}
 
 template <typename K>
 KernelInfo Launcher<K>::info(int variant) {
@@ -126,7 +137,8 @@ long long Launcher<K>::tile_count(int variant, const void *buf, long long begin,
 }
 
 template <typename K>
-cudaError_t Launcher<K>::occupancy(int variant, int cutoff, int *tile_ctas, int *small_ctas) {
+cudaError_t Launcher<K>::occupancy(int variant, int cutoff, int nt, int *tile_ctas,
+                                   int *small_ctas) {
   cudaError_t e = with_shape<K>(variant, [&](auto s) {
     using S = decltype(s);
     void (*fn)(SortParams) = nullptr;
@@ -135,11 +147,11 @@ cudaError_t Launcher<K>::occupancy(int variant, int cutoff, int *tile_ctas, int 
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(tile_ctas, fn, S::NT, S::SMEM);
   });
   if (e != cudaSuccess) return e;
-  auto sk = dev::small_kernel<K>;
-  const size_t smem = small_smem_bytes(cutoff);
-  e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*sk)(SortParams) = nullptr;
+  size_t smem = 0;
+  e = small_kernel_of<K>(nt, cutoff, &sk, &smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(small_ctas, sk, dev::kSmallThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(small_ctas, sk, small_threads_of(nt), smem);
 }
 
 template <typename K>
@@ -162,6 +174,36 @@ cudaError_t Launcher<K>::tiles(const SortParams &p, int variant, int grid, cudaS
     fn<<<grid, S::NT, S::SMEM, st>>>(p);
     return cudaGetLastError();
   });
+}
+
+// The fused tile kernel (queue form, CTA shape 2: 256 threads), with its dynamic shared
+// memory for the finisher of `cutoff`-key items allowed.
+template <typename K>
+cudaError_t fused_kernel_of(int cutoff, void (**fn)(SortParams), size_t *smem) {
+  using S = ShapeOf<K, kFusedVariant>;
+  static_assert(S::FORM == 0 && S::NT == 256, "fused shape");
+  *fn = dev::tile_kernel<K, S::NT, S::IPT, true>;
+  *smem = dev::fuse_smem_bytes<K>(cutoff, S::NT);
+  return cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+}
+
+template <typename K>
+cudaError_t Launcher<K>::fused_occupancy(int cutoff, int *ctas) {
+  void (*fn)(SortParams) = nullptr;
+  size_t smem = 0;
+  cudaError_t e = fused_kernel_of<K>(cutoff, &fn, &smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, 256, smem);
+}
+
+template <typename K>
+cudaError_t Launcher<K>::tiles_fused(const SortParams &p, int grid, cudaStream_t st) {
+  void (*fn)(SortParams) = nullptr;
+  size_t smem = 0;
+  cudaError_t e = fused_kernel_of<K>(p.cutoff, &fn, &smem);
+  if (e != cudaSuccess) return e;
+  fn<<<grid, 256, smem, st>>>(p);
+  return cudaGetLastError();
 }
 
 // part_kernel of CTA shape `shape`, with its dynamic shared memory allowed.
@@ -423,11 +465,11 @@ cudaError_t Launcher<K>::exact(const void *in, void *out, long long n, long long
 
 template <typename K>
 cudaError_t Launcher<K>::smalls(const SortParams &p, int grid, cudaStream_t s) {
-  auto sk = dev::small_kernel<K>;
-  const size_t smem = small_smem_bytes(p.cutoff);
-  cudaError_t e = cudaFuncSetAttribute(sk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  void (*sk)(SortParams) = nullptr;
+  size_t smem = 0;
+  cudaError_t e = small_kernel_of<K>(p.small_threads, p.cutoff, &sk, &smem);
   if (e != cudaSuccess) return e;
-  sk<<<grid, dev::kSmallThreads, smem, s>>>(p);
+  sk<<<grid, small_threads_of(p.small_threads), smem, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -157,6 +157,25 @@ def test_tile_shapes_and_tuning_fields(lib):
         assert ks.ksort_get_tuning(code)["sort_reserve"] == -1
         ks.ksort_set_tuning(code, sort_reserve=before["sort_reserve"])
         assert ks.ksort_get_tuning(code) == before
+        assert before["finish_in_tiles"] == -1 or 1 <= before["finish_in_tiles"] <= 4096
+        for bad in (-2, 4097):
+            with pytest.raises(ks.KSortError):
+                ks.ksort_set_tuning(code, finish_in_tiles=bad)
+        ks.ksort_set_tuning(code, finish_in_tiles=32)
+        assert ks.ksort_get_tuning(code)["finish_in_tiles"] == 32
+        ks.ksort_set_tuning(code, finish_in_tiles=-1)
+        assert ks.ksort_get_tuning(code)["finish_in_tiles"] == -1
+        ks.ksort_set_tuning(code, finish_in_tiles=before["finish_in_tiles"])
+        assert ks.ksort_get_tuning(code) == before
+        assert before["finisher_threads"] in (256, 512, 1024)
+        for bad in (-1, 128, 300, 2048):
+            with pytest.raises(ks.KSortError):
+                ks.ksort_set_tuning(code, finisher_threads=bad)
+        for nt in (512, 1024, 256):
+            ks.ksort_set_tuning(code, finisher_threads=nt)
+            assert ks.ksort_get_tuning(code)["finisher_threads"] == nt
+        ks.ksort_set_tuning(code, finisher_threads=before["finisher_threads"])
+        assert ks.ksort_get_tuning(code) == before
         # every ring configuration stages the same bytes per tile for 4- and 8-byte keys
         keyb = 8 if code == ks.F64 else 4
         for form in (1, 2, 3, 4):

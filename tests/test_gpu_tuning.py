@@ -28,7 +28,8 @@ def restore(ks):
     for c, t in saved.items():
         ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
                             tile_shape=t["tile_shape"], partition_form=t["partition_form"],
-                            sort_reserve=t["sort_reserve"])
+                            sort_reserve=t["sort_reserve"], finish_in_tiles=t["finish_in_tiles"],
+                            finisher_threads=t["finisher_threads"])
 
 
 def _sort(ks, a):
@@ -94,6 +95,47 @@ def test_cutoff_and_finisher_extremes(ref, ks, restore, cutoff, ctas):
         for pattern in ("uniform", "distinct16"):
             a = gen.make(pattern, dtype, 40_000, gen.seed_for(6, 11, c))
             assert _sort(ks, a).tobytes() == _oracle(ref, a).tobytes(), (dtype, pattern)
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("cutoff", [2, 33, 2048, 16384])
+def test_finisher_threads(ref, ks, restore, threads, cutoff):
+    """Finisher CTAs of every size, from the smallest cutoff to the largest (where the
+    CTA-wide partitions run before the warps take over), on random and duplicate-heavy
+    inputs and on batches with empty and one-key arrays."""
+    for dtype, code in DTYPES.items():
+        c = min(cutoff, ks.ksort_max_cutoff(code))
+        ks.ksort_set_tuning(code, cutoff=c, finisher_threads=threads)
+        assert ks.ksort_get_tuning(code)["finisher_threads"] == threads
+        for pattern in ("uniform", "distinct16", "quantized15"):
+            a = gen.make(pattern, dtype, 60_001, gen.seed_for(6, 12, c + threads))
+            assert _sort(ks, a).tobytes() == _oracle(ref, a).tobytes(), (dtype, pattern)
+    ks.ksort_set_tuning(ks.F32, cutoff=min(cutoff, 16384), finisher_threads=threads)
+    lengths = gen.batched_lengths(300, 1, 40_000, seed=gen.seed_for(6, 13, threads))
+    lengths[0] = 0
+    lengths[7] = 1
+    off = gen.offsets_from_lengths(lengths)
+    flat = gen.uniform_f32(gen.seed_for(6, 14, threads), int(off[-1]))
+    want = flat.copy()
+    ref.sort_batched(want, off)
+    import torch
+    keys = torch.from_numpy(flat.copy()).cuda()
+    ks.sort_batched_(keys, torch.from_numpy(off).cuda())
+    assert ks.ksort_get_device_error() == 0
+    assert keys.cpu().numpy().tobytes() == want.tobytes()
+
+
+@pytest.mark.parametrize("threads", [512, 1024])
+def test_finisher_threads_nan(ks, restore, threads):
+    """Items holding a NaN take the level-by-level path with the larger CTA as well."""
+    ks.ksort_set_tuning(ks.F32, finisher_threads=threads)
+    rng = np.random.default_rng(threads)
+    a = rng.random(300_001).astype(np.float32)
+    a[rng.random(a.size) < 0.02] = np.nan
+    got = _sort(ks, a)
+    assert np.sort(got.view(np.uint32)).tobytes() == np.sort(a.view(np.uint32)).tobytes()
+    v = got[~np.isnan(got)]
+    assert np.all(v[1:] >= v[:-1])
 
 
 def test_autotuner_searches_applies_and_caches(ks, restore, tmp_path, monkeypatch):
