@@ -59,6 +59,18 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start before the previous kernel in the stream has finished;
+// grid_dep_wait() blocks until that kernel has completed and its memory is visible (a
+// no-op in a kernel launched without the attribute). grid_dep_launch() lets the next
+// such kernel start launching.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -547,23 +559,33 @@ __device__ __forceinline__ int warp_partition(const K *X, K *Y, int s, int n, K 
   const unsigned lt = lanemask_lt();
   const int e = s + n;
   int L = 0, G = 0;
-  for (int i0 = s + 1; i0 < e; i0 += 128) {
+  int i0 = s + 1;
+  // groups of four full chunks: every lane has a key, so the >= lanes are the others
+  for (; i0 + 128 <= e; i0 += 128) {
     K x[4];
-    bool v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = X[i0 + 32 * u + lane];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int i = i0 + 32 * u + lane;
-      v[u] = i < e;
-      x[u] = v[u] ? X[i] : K(0);
+      const bool l = goes_left(key, x[u]);
+      const unsigned ml = __ballot_sync(kFull, l);
+      const int rl = __popc(ml & lt);
+      Y[l ? s + L + rl : e - 1 - G - (lane - rl)] = x[u];
+      const int c = __popc(ml);
+      L += c;
+      G += 32 - c;
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool l = v[u] && goes_left(key, x[u]);
-      const unsigned ml = __ballot_sync(kFull, l), mg = __ballot_sync(kFull, v[u] && !l);
-      if (v[u]) Y[l ? s + L + __popc(ml & lt) : e - 1 - G - __popc(mg & lt)] = x[u];
-      L += __popc(ml);
-      G += __popc(mg);
-    }
+  }
+  // the rest one chunk at a time (the same order, so the same layout)
+  for (; i0 < e; i0 += 32) {
+    const int i = i0 + lane;
+    const bool v = i < e;
+    const K x = v ? X[i] : K(0);
+    const bool l = v && goes_left(key, x);
+    const unsigned ml = __ballot_sync(kFull, l), mg = __ballot_sync(kFull, v && !l);
+    if (v) Y[l ? s + L + __popc(ml & lt) : e - 1 - G - __popc(mg & lt)] = x;
+    L += __popc(ml);
+    G += __popc(mg);
   }
   __syncwarp();
   return L;
@@ -697,9 +719,17 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
   return q.bad == 0;
 }
 
+// Largest final segment of the marked form (2 .. 32): its closed form costs one compare
+// per key of the segment, and segments above it are partitioned by a warp.
+#ifndef KSORT_MARK_LEAF
+#define KSORT_MARK_LEAF 16
+#endif
+constexpr int kMarkLeaf = KSORT_MARK_LEAF;
+static_assert(kMarkLeaf >= 2 && kMarkLeaf <= 32, "a marked segment spans at most two words");
+
 // Marked form of the finisher, for sub-arrays without NaN keys (the closed form of a
 // leaf needs a total order). The partitions run as in smem_ksort, but a final segment
-// (a key at its index, a one-key side, a leaf of 2..kLeaf keys) is not finished where it
+// (a key at its index, a one-key side, a leaf of 2..kMarkLeaf keys) is not finished where it
 // appears: its first index is marked in the bitmap `seg`, and in `par` when its keys are
 // in B. Bit m of `seg` closes the last segment. Once every partition is done, each
 // index of the sub-array finds its segment from the marks (a segment spans at most 32
@@ -712,17 +742,17 @@ __device__ __forceinline__ void seg_mark(unsigned *bits, int i) {
   atomicOr(&bits[i >> 5], 1u << (i & 31));
 }
 
-// A final side [cs, cs + cn) of 1..kLeaf keys, in B when cp is 1.
+// A final side [cs, cs + cn) of 1..kMarkLeaf keys, in B when cp is 1.
 __device__ __forceinline__ void mark_final(unsigned *seg, unsigned *par, int cs, int cn, int cp) {
   if (cn < 1) return;
   seg_mark(seg, cs);
   if (cp) seg_mark(par, cs);
 }
 
-template <typename K, int NT>
+template <typename K, int NT, typename Pre>
 __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
                                   K *__restrict__ out, int m, SmallShared &q,
-                                  unsigned long long *segments) {
+                                  unsigned long long *segments, Pre &&pre) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int words = (m >> 5) + 2;
   for (int i = tid; i < kSmallQueue; i += NT) q.ring[i] = 0u;
@@ -738,10 +768,10 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
     q.nbig = 0;
   }
   bsync();
-  unsigned long long nseg = m <= kLeaf ? 1 : 0;
+  unsigned long long nseg = m <= kMarkLeaf ? 1 : 0;
   if (tid == 0) {
     seg_mark(seg, m);
-    if (m <= kLeaf) mark_final(seg, par, 0, m, 0);
+    if (m <= kMarkLeaf) mark_final(seg, par, 0, m, 0);
     else if (m > kBlockSegment) q.big[q.nbig++] = seg_pack(0, m, 0);
     else small_push(q, 0, m, 0);
   }
@@ -765,13 +795,13 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
       for (int c = 0; c < 2; ++c) {
         const int cs = c ? s + L + 1 : s, cn = c ? n - L - 1 : L;
         if (cn > kBlockSegment) q.big[q.nbig++] = seg_pack(cs, cn, cp);
-        else if (cn > kLeaf) small_push(q, cs, cn, cp);
+        else if (cn > kMarkLeaf) small_push(q, cs, cn, cp);
         else mark_final(seg, par, cs, cn, cp);
       }
     }
     bsync();
   }
-  // warp-level Steps 1-6 on the queued segments (all above kLeaf keys)
+  // warp-level Steps 1-6 on the queued segments (all above kMarkLeaf keys)
   while (true) {
     unsigned e = 0;
     if (lane == 0) e = small_pop(q);
@@ -788,12 +818,12 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
       if (lane == 0) {
         A[s + L] = key;  // Step 4: final index
         seg_mark(seg, s + L);
-        if (ln <= kLeaf) mark_final(seg, par, ls, ln, cp);
-        if (rn <= kLeaf) mark_final(seg, par, rs, rn, cp);
+        if (ln <= kMarkLeaf) mark_final(seg, par, ls, ln, cp);
+        if (rn <= kMarkLeaf) mark_final(seg, par, rs, rn, cp);
       }
-      // Steps 5-6: of two sides above kLeaf keys the smaller is queued and the warp
+      // Steps 5-6: of two sides above kMarkLeaf keys the smaller is queued and the warp
       // keeps the other
-      const bool bl = ln > kLeaf, br = rn > kLeaf;
+      const bool bl = ln > kMarkLeaf, br = rn > kMarkLeaf;
       if (bl && br) {
         if (lane == 0) {
           if (ln < rn) small_push(q, ls, ln, cp);
@@ -815,7 +845,9 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
     }
   }
   bsync();
-  // every index: its segment from the marks, its key to the final index
+  // every index: its segment from the marks, its key to the final index; thread 0 first
+  // runs `pre` (the claim of the next item), which overlaps the other warps' windows
+  if (tid == 0) pre();
   const unsigned le = lane == 31 ? kFull : ((2u << lane) - 1u);
   const int nwin = (m + 31) >> 5;
   bool broken = false;
@@ -828,7 +860,7 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
     const int e0 = above ? (w << 5) + __ffs(above) - 1
                          : (nxt ? ((w + 1) << 5) + __ffs(nxt) - 1 : -1);
     if (i >= m) continue;
-    if (s0 < 0 || e0 < 0 || e0 - s0 > kLeaf) {  // marks do not cover i: report, skip
+    if (s0 < 0 || e0 < 0 || e0 - s0 > kMarkLeaf) {  // marks do not cover i: report, skip
       broken = true;
       continue;
     }
@@ -1030,13 +1062,14 @@ __device__ __forceinline__ int claim_small(const SortParams &p, unsigned epoch, 
 
 // A CTA of NT threads, any phase: the small item `it` (index h) is loaded into shared
 // memory and finished there by smem_ksort_marked, or by smem_ksort when it holds a NaN
-// key; its keys end in buffer 0. Ends with a CTA barrier.
-template <typename K, int NT>
-__device__ __forceinline__ void finish_small_item(const SortParams &p, const Item &it, long long h,
+// key; its keys end in buffer 0. Thread 0 runs `pre` once on the way (the next item's
+// claim), and the closing CTA barrier makes what it wrote visible.
+template <typename K, int NT, typename Pre>
+__device__ __forceinline__ void finish_small_item(const SortParams &p, const Item it, long long h,
                                                   K *buf0, const K *buf1, const SmallSmem<K> &sm,
                                                   SmallShared &q, unsigned long long *st_small,
                                                   unsigned long long *st_small_keys,
-                                                  unsigned long long *st_segs) {
+                                                  unsigned long long *st_segs, Pre &&pre) {
   const int tid = threadIdx.x;
   const K *src = ((it.flags & kItemScratch) ? buf1 : buf0) + it.begin;
   const int m = (int)(it.end - it.begin);
@@ -1046,11 +1079,14 @@ __device__ __forceinline__ void finish_small_item(const SortParams &p, const Ite
     sm.A[e] = v;
     nan |= key_is_nan(v);
   }
-  const bool ok = __syncthreads_or(nan)
-                      ? smem_ksort<K, NT>(sm.A, sm.B, sm.leaf_lists, buf0 + it.begin, m, q,
-                                          st_segs)
-                      : smem_ksort_marked<K, NT>(sm.A, sm.B, sm.seg, sm.par, buf0 + it.begin, m,
-                                                 q, st_segs);
+  bool ok;
+  if (__syncthreads_or(nan)) {
+    ok = smem_ksort<K, NT>(sm.A, sm.B, sm.leaf_lists, buf0 + it.begin, m, q, st_segs);
+    if (tid == 0) pre();
+  } else {
+    ok = smem_ksort_marked<K, NT>(sm.A, sm.B, sm.seg, sm.par, buf0 + it.begin, m, q, st_segs,
+                                  pre);
+  }
   if (tid == 0) {
     if (!ok) raise_error(p.ctl, kDevInternal, 0x600000000ull | (unsigned)h);
     ++*st_small;
@@ -1239,6 +1275,8 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
   K *const buf0 = static_cast<K *>(p.keys);
   K *const buf1 = static_cast<K *>(p.scratch);
   Control *ctl = p.ctl;
+  grid_dep_wait();    // the seed (or the previous launch) is complete
+  grid_dep_launch();  // the finisher may start launching as CTAs leave
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const unsigned lt = lanemask_lt();
@@ -1302,7 +1340,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       const SmallSmem<K> sm(fuse_smem + (sizeof(SmallShared) + 15) / 16 * 16, p.cutoff, NT);
       if (sh.r == 2) {  // a small item, taken while other CTAs wait for tiles
         finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, q, &st_small, &st_small_keys,
-                                 &st_segs);
+                                 &st_segs, [] {});
         continue;
       }
       if (sh.r == 0) {  // the tile passes are over: drain the small list
@@ -1311,7 +1349,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
           __syncthreads();
           if (sh.r <= 0) break;
           finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, q, &st_small,
-                                   &st_small_keys, &st_segs);
+                                   &st_small_keys, &st_segs, [] {});
         }
         break;
       }
@@ -1811,6 +1849,8 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_ws_kernel(SortPa
   __shared__ WsShared<ND> sh;
   K *const buf0 = static_cast<K *>(p.keys);
   Control *ctl = p.ctl;
+  grid_dep_wait();
+  grid_dep_launch();
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
 
@@ -2631,12 +2671,6 @@ __global__ void __launch_bounds__(kExactThreads) exact_place_kernel(
 // the same launch may still be reading the sub-array, so the key is recorded in
 // wave_fin and written to buffer 0 by the next launch (an odd level's count, or the
 // hand-off); odd levels read buffer 1 and write the key at once.
-__device__ __forceinline__ void grid_dep_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-__device__ __forceinline__ void grid_dep_launch() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Keys per CTA span: equal shares of the level, at least one tile each.
 __device__ __forceinline__ long long wave_span(long long keys, int grid, int tile) {
@@ -3245,16 +3279,19 @@ __global__ void __launch_bounds__(NT) small_kernel(SortParams p) {
   K *const buf0 = static_cast<K *>(p.keys);
   K *const buf1 = static_cast<K *>(p.scratch);
   Control *ctl = p.ctl;
+  grid_dep_wait();  // the tile passes are complete
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const int tid = threadIdx.x;
   const SmallSmem<K> sm(smem, p.cutoff, NT);
   unsigned long long st_small = 0, st_small_keys = 0, st_segs = 0;
-  while (true) {
-    if (tid == 0) sh.r = claim_small(p, epoch, &sh.h, &sh.it);
-    __syncthreads();
-    if (sh.r <= 0) break;
-    finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, sh.q, &st_small, &st_small_keys,
-                             &st_segs);
+  if (tid == 0) sh.r = claim_small(p, epoch, &sh.h, &sh.it);
+  __syncthreads();
+  while (sh.r > 0) {
+    const Item it = sh.it;
+    const long long h = sh.h;
+    __syncthreads();  // every thread holds the item before thread 0 claims the next
+    finish_small_item<K, NT>(p, it, h, buf0, buf1, sm, sh.q, &st_small, &st_small_keys,
+                             &st_segs, [&] { sh.r = claim_small(p, epoch, &sh.h, &sh.it); });
   }
   if (tid == 0) {
     if (st_small) atomicAdd(&ctl->small_items, st_small);
@@ -3286,6 +3323,7 @@ template <typename K, int TILE>
 __global__ void seed_kernel(SortParams p) {
   __shared__ unsigned epoch_sh;
   Control *ctl = p.ctl;
+  grid_dep_launch();  // the tile kernel may start launching; it waits for this one
   if (threadIdx.x == 0) {
     unsigned ep = ctl->epoch + 1u;
     if (ep == 0u || ep >= kMaxEpoch) ep = 1u;

@@ -154,6 +154,25 @@ cudaError_t Launcher<K>::occupancy(int variant, int cutoff, int nt, int *tile_ct
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(small_ctas, sk, small_threads_of(nt), smem);
 }
 
+// Launches fn<<<grid, block, smem, s>>>(p) under programmatic stream serialization: its
+// CTAs may become resident while the previous kernel in the stream finishes, and wait
+// in grid_dep_wait() until that kernel's memory is complete, so the launch latency
+// overlaps the previous kernel's tail.
+inline cudaError_t launch_after(void (*fn)(SortParams), int grid, int block, size_t smem,
+                                const SortParams &p, cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, p);
+}
+
 template <typename K>
 cudaError_t Launcher<K>::seed(const SortParams &p, int variant, cudaStream_t st) {
   with_shape<K>(variant, [&](auto s) {
@@ -171,8 +190,7 @@ cudaError_t Launcher<K>::tiles(const SortParams &p, int variant, int grid, cudaS
     void (*fn)(SortParams) = nullptr;
     cudaError_t e = tile_kernel_of<K, S>(&fn);
     if (e != cudaSuccess) return e;
-    fn<<<grid, S::NT, S::SMEM, st>>>(p);
-    return cudaGetLastError();
+    return launch_after(fn, grid, S::NT, S::SMEM, p, st);
   });
 }
 
@@ -202,8 +220,7 @@ cudaError_t Launcher<K>::tiles_fused(const SortParams &p, int grid, cudaStream_t
   size_t smem = 0;
   cudaError_t e = fused_kernel_of<K>(p.cutoff, &fn, &smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, 256, smem, st>>>(p);
-  return cudaGetLastError();
+  return launch_after(fn, grid, 256, smem, p, st);
 }
 
 // part_kernel of CTA shape `shape`, with its dynamic shared memory allowed.
@@ -311,8 +328,7 @@ cudaError_t Launcher<K>::ring_partition(const SortParams &p, int cfg, int grid, 
     void (*fn)(SortParams) = nullptr;
     cudaError_t e = ring_kernel_of<K, C>(&fn);
     if (e != cudaSuccess) return e;
-    fn<<<grid, C::NT, C::SMEM, st>>>(p);
-    return cudaGetLastError();
+    return launch_after(fn, grid, C::NT, C::SMEM, p, st);
   });
 }
 
@@ -469,8 +485,7 @@ cudaError_t Launcher<K>::smalls(const SortParams &p, int grid, cudaStream_t s) {
   size_t smem = 0;
   cudaError_t e = small_kernel_of<K>(p.small_threads, p.cutoff, &sk, &smem);
   if (e != cudaSuccess) return e;
-  sk<<<grid, small_threads_of(p.small_threads), smem, s>>>(p);
-  return cudaGetLastError();
+  return launch_after(sk, grid, small_threads_of(p.small_threads), smem, p, s);
 }
 
 }  // namespace ksort

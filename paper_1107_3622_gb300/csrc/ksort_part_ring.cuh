@@ -286,6 +286,8 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
   auto slot = [&](int s) { return reinterpret_cast<K *>(ring_smem + (size_t)s * C::SLOT); };
 
   Control *const ctl = p.ctl;
+  grid_dep_wait();    // the previous launch in the stream is complete
+  grid_dep_launch();  // the next one may start launching as CTAs leave
   unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch) + 1u;
   if (epoch == 0u || epoch >= kMaxEpoch) epoch = 1u;
   const K *const src = static_cast<const K *>(p.keys);

@@ -123,6 +123,8 @@ __global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortPar
   __shared__ TileRingShared<NDW, S> sh;
   auto slot = [&](int s) { return reinterpret_cast<K *>(tring_smem + (size_t)s * C::SLOT); };
   Control *const ctl = p.ctl;
+  grid_dep_wait();
+  grid_dep_launch();
   const unsigned epoch = *reinterpret_cast<volatile unsigned *>(&ctl->epoch);
   const unsigned long long limit = p.spin_limit_ns;
   volatile int *const stop = &sh.stop;
