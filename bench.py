@@ -21,7 +21,7 @@ Also reported on the same line:
   serving        10,000 Poisson requests (log-uniform 1e3..1e7 keys, half float32, half
                  uint32) in page-locked host memory, served by continuous batching on a
                  stream pool, admitted into an HBM arena sized from free memory, at 0.8 x
-                 the measured capacity with copies: keys/s, p50/p99 latency from arrival
+                 the server's measured burst capacity: keys/s, p50/p99 latency from arrival
                  (copies included), HBM budget and peak bytes in use, and every result
                  checked equal to the same request sorted alone
   clocks         SM clock and throttle reasons sampled during the timed region
@@ -64,6 +64,8 @@ PAPER_TABLE1_S = {100_000: 0.0157, 500_000: 0.0811, 1_000_000: 0.1877, 2_500_000
 L2_FLUSH_BYTES = 256 << 20
 WORKLOAD = "ksort_sort n=7e6 float32 U[0,1] (Table 1 size)"
 DEVICE_SOURCES = ("paper_1107_3622_gb300/csrc/ksort_device.cuh",
+                  "paper_1107_3622_gb300/csrc/ksort_part_ring.cuh",
+                  "paper_1107_3622_gb300/csrc/ksort_tile_ring.cuh",
                   "paper_1107_3622_gb300/csrc/ksort_launch.cuh",
                   "paper_1107_3622_gb300/csrc/ksort_internal.h")
 
@@ -96,7 +98,56 @@ def parse_args(argv=None):
                     help="requests of the serving run (0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="time budget of the cpu_baseline sample")
+    ap.add_argument("--profile", choices=("sort", "partition", "batched"),
+                    help="for profilers: run one workload (--n keys, or --arrays arrays of "
+                         "the batch mix) --warmup + 1 times, untimed, under the library "
+                         "defaults or the --tile-shape / --cutoff given, then exit")
+    ap.add_argument("--arrays", type=int, default=4096,
+                    help="arrays of the batch in --profile batched")
     return ap.parse_args(argv)
+
+
+def run_profile(args):
+    """One workload, --warmup + 1 calls, nothing timed: a fixed target for ncu captures
+    (the last call is the one to capture; each call checks its result)."""
+    import torch
+    import paper_1107_3622_gb300 as ks
+    from paper_1107_3622_gb300 import autotune
+    torch.cuda.set_device(0)
+    ks.load()
+    autotune.reset(ks.F32)
+    ks.ksort_set_tuning(ks.F32, cutoff=args.cutoff, tile_shape=args.tile_shape)
+    if args.profile == "batched":
+        lengths = gen.batched_lengths()[: args.arrays]
+        off = gen.offsets_from_lengths(lengths)
+        n = int(off[-1])
+        offs = torch.from_numpy(off).cuda()
+    else:
+        n = args.n
+    src = gen.uniform_torch("f32", gen.seed_for(1, 6, 0), n, device="cuda")
+    keys = torch.empty_like(src)
+    idx = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ks.ksort_reserve_workspace(ks.F32, n, args.arrays if args.profile == "batched" else 1)
+    for _ in range(args.warmup + 1):
+        if args.profile == "partition":
+            ks.ksort_partition_out(ks.F32, src, keys, n, idx)
+        else:
+            keys.copy_(src)
+            if args.profile == "sort":
+                ks.ksort_sort(ks.F32, keys, n)
+            else:
+                ks.ksort_sort_batched(ks.F32, keys, offs, len(lengths), n)
+        torch.cuda.synchronize()
+        if ks.ksort_get_device_error():
+            raise RuntimeError("device error in the profiled workload")
+    if args.profile == "partition":
+        i = int(idx.item())
+        if not (bool((keys[:i] < keys[i]).all()) and bool((keys[i + 1:] >= keys[i]).all())):
+            raise RuntimeError("partition check failed")
+    elif not bool((keys[1:] >= keys[:-1]).all()) and args.profile == "sort":
+        raise RuntimeError("unsorted output")
+    print(json.dumps({"profile": args.profile, "n": n, "calls": args.warmup + 1,
+                      "tuning": ks.ksort_get_tuning(ks.F32), "stats": ks.ksort_get_stats()}))
 
 
 # ----------------------------------------------------------------------------- dist
@@ -260,7 +311,7 @@ def device_source_hash():
     return h.hexdigest()[:16]
 
 
-TILE_KERNELS = {0: "tile_kernel", 1: "tile_pipe_kernel", 2: "tile_ws_kernel",
+TILE_KERNELS = {0: "tile_kernel", 1: "tile_ring_kernel", 2: "tile_ws_kernel",
                 3: "wave_scatter_kernel"}
 
 
@@ -817,8 +868,8 @@ def run_serving(ks, count: int, tuning: dict):
     """Serving configuration: `count` Poisson requests, sizes log-uniform in
     [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys in page-locked host memory,
     copied into an HBM arena at admission and back when sorted; the arena is sized from
-    the HBM left free after the slot workspaces. The rate is 0.8 x the capacity measured
-    on the same size mix with the copies in line, / mean keys per request."""
+    the HBM left free after the slot workspaces. The rate is 0.8 x the server's own
+    throughput on a burst of 500 requests of the same mix, / mean keys per request."""
     import torch
     from paper_1107_3622_gb300 import serving
     # serving batches take the batched form's tuning, for both 4-byte key types
@@ -829,13 +880,14 @@ def run_serving(ks, count: int, tuning: dict):
                             finish_in_tiles=tuning.get("finish_in_tiles", -1),
                             finisher_threads=tuning.get("finisher_threads", 256))
     cap = serving.measure_capacity()
-    rate = 0.8 * cap["with_copies_keys_per_s"] / serving.mean_length()
-    reqs = serving.poisson_requests(count, rate)
     torch.cuda.empty_cache()
+    srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
+    burst = serving.burst_capacity(srv)
+    rate = 0.8 * burst / serving.mean_length()
+    reqs = serving.poisson_requests(count, rate)
     t0 = time.perf_counter()
     pools = serving.build_pools(reqs)
     gen_s = time.perf_counter() - t0
-    srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
     res = srv.run(reqs, pools)
     out = res.summary()
     srv.close()
@@ -851,8 +903,12 @@ def run_serving(ks, count: int, tuning: dict):
     if ks.ksort_get_device_error():
         raise RuntimeError("device error in the serving check")
     out.update({"rate_per_s": round(rate, 1),
-                "capacity_keys_per_s": round(cap["with_copies_keys_per_s"], 1),
-                "capacity_sort_only_keys_per_s": round(cap["sort_keys_per_s"], 1),
+                "capacity_keys_per_s": round(burst, 1),
+                "capacity": "the server's own throughput on 500 requests of the mix arriving at "
+                            "once (copies, admission and slot overlap included); the rate is "
+                            "0.8 x that / mean keys per request",
+                "one_batch_with_copies_keys_per_s": round(cap["with_copies_keys_per_s"], 1),
+                "one_batch_sort_only_keys_per_s": round(cap["sort_keys_per_s"], 1),
                 "slots": 4, "slot_keys": 1 << 27,
                 "host_pool_bytes": pools.nbytes(),
                 "alone_vs_mix_identical": mismatches == 0, "checked": len(reqs),
@@ -1016,6 +1072,9 @@ def main(argv=None):
         return 0
     if args.sweep:
         print(json.dumps(run_sweep(args)), flush=True)
+        return 0
+    if args.profile:
+        run_profile(args)
         return 0
     dist = Dist(args.gpus)
     try:

@@ -456,6 +456,19 @@ def sort_alone(r: Request):
     return t
 
 
+def burst_capacity(server: "Server", count: int = 500, lo: int = 1_000, hi: int = 10_000_000,
+                   seed: int | None = None) -> float:
+    """Keys/s the server sustains on `count` requests of the mix that all arrive at once:
+    its own throughput at saturation, copies, admission and slot overlap included."""
+    if seed is None:
+        seed = gen.seed_for(5, 4, 0)
+    reqs = poisson_requests(count, 1e12, lo, hi, seed=seed)
+    with build_pools(reqs) as pools:
+        res = server.run(reqs, pools)
+    span = max(r.done_s for r in reqs) - min(r.arrival_s for r in reqs)
+    return res.keys / span
+
+
 def measure_capacity(count: int = 256, lo: int = 1_000, hi: int = 10_000_000,
                      max_keys: int = 1 << 28) -> dict:
     """Keys/s of one ksort_sort_batched over a batch drawn from the serving size mix
@@ -499,4 +512,4 @@ def measure_capacity(count: int = 256, lo: int = 1_000, hi: int = 10_000_000,
 
 __all__ = ["Request", "Planner", "Arena", "Batch", "Server", "RunResult", "HostPools",
            "poisson_requests", "build_pools", "request_keys", "sort_alone",
-           "measure_capacity", "mean_length", "dtype_code"]
+           "measure_capacity", "burst_capacity", "mean_length", "dtype_code"]
