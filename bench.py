@@ -88,6 +88,9 @@ def parse_args(argv=None):
                     help="inputs of --sweep: U[0,1], or U[0,1] on 2**15 levels")
     ap.add_argument("--sweep-oracle-reps", type=int, default=2,
                     help="oracle repetitions per size in --sweep (0 skips the oracle)")
+    ap.add_argument("--sweep-defaults", action="store_true",
+                    help="time --sweep under the library defaults instead of the autotuner's "
+                         "choice for each size")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the library's default tuning instead of the autotuned one")
     ap.add_argument("--tile-shape", type=int, default=0,
@@ -928,9 +931,11 @@ def run_serving(ks, count: int, tuning: dict):
 
 def run_sweep(args):
     """Table 1 sizes, float32 and float64 U[0,1], 20 seeded repetitions each (rep r =
-    seed rep r): mean ksort_sort time (CUDA events, L2 flushed and input restored before
-    every run), keys/s, algorithmic GB/s of the sort and its fraction of the measured HBM
-    peak, every output checked sorted; the oracle's mean time on a few of the same arrays."""
+    seed rep r), each size under the autotuner's choice for it (or the library defaults
+    with --sweep-defaults): mean ksort_sort time (CUDA events, L2 flushed and input
+    restored before every run), keys/s, algorithmic GB/s of the sort and its fraction of
+    the measured HBM peak, the phase split, every output checked sorted; the oracle's mean
+    time on a few of the same arrays."""
     import torch
     import paper_1107_3622_gb300 as ks
     from paper_1107_3622_gb300 import statbound
@@ -945,10 +950,16 @@ def run_sweep(args):
     # the library's phase events split every timed sort into seed, partition passes and
     # finisher (they add a few microseconds per call; the means below include them)
     ks.ksort_set_phase_timing(True)
+    from paper_1107_3622_gb300 import autotune
     for name, code, kb in (("f32", ks.F32, 4), ("f64", ks.F64, 8)):
         ks.ksort_reserve_workspace(code, max(gen.TABLE1_SIZES), 1)
         for si, n in enumerate(gen.TABLE1_SIZES):
             cfg = 1 if name == "f32" else 2
+            if args.sweep_defaults:
+                autotune.reset(code)
+            else:  # the autotuner's choice for this size (searched here, or cached)
+                autotune.autotune("sort", code, n=n, reps=3)
+            ks.ksort_reserve_workspace(code, max(gen.TABLE1_SIZES), 1)
             ms, algo, passes = [], [], []
             for r in range(reps):
                 if args.sweep_pattern == "uniform":
@@ -984,6 +995,8 @@ def run_sweep(args):
                    # tile passes a key goes through on average (large_keys / n): the
                    # number of global partition levels, counted by the library
                    "tile_levels": round(statistics.fmean(passes), 2),
+                   "tuning": {k: v for k, v in ks.ksort_get_tuning(code).items()
+                              if k not in ("spin_limit_ms", "medium_tiles", "partition_form")},
                    "phases_ms": {k: round(statistics.fmean(p[i] for p in ph), 4)
                                  for i, k in enumerate(("seed", "partition_passes", "finisher"))}
                                 if ph else None,
