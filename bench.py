@@ -693,7 +693,8 @@ def run_partition_pass(ks, n, peak, peak_src, args):
                         wave_levels=saved.get("wave_levels", -1),
                         partition_form=saved["partition_form"],
                         finish_in_tiles=saved.get("finish_in_tiles", -1),
-                        finisher_threads=saved.get("finisher_threads", 256))
+                        finisher_threads=saved.get("finisher_threads", 256),
+                        cluster_sort=saved.get("cluster_sort", -1))
     return {"kernel": f"ksort_partition_out: {kname} <float>, {launches}",
             "n": n, "tuning": tuned,
             "us_per_launch": round(ms * 1e3, 2),
@@ -810,7 +811,8 @@ def run_batched(ks, args, peak, peak_src):
         ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"], tile_shape=sort_tuning["tile_shape"],
                             wave_levels=sort_tuning.get("wave_levels", -1),
                             finish_in_tiles=sort_tuning.get("finish_in_tiles", -1),
-                            finisher_threads=sort_tuning.get("finisher_threads", 256))
+                            finisher_threads=sort_tuning.get("finisher_threads", 256),
+                            cluster_sort=sort_tuning.get("cluster_sort", -1))
         el = autotune.autotune("sort", ks.F32, n=mean_len, reps=3)
         loop_info = {"autotuned": True, "for_n": mean_len, "cached": el["cached"]}
     else:
@@ -819,7 +821,8 @@ def run_batched(ks, args, peak, peak_src):
                             tile_shape=sort_tuning["tile_shape"],
                             wave_levels=sort_tuning.get("wave_levels", -1),
                             finish_in_tiles=sort_tuning.get("finish_in_tiles", -1),
-                            finisher_threads=sort_tuning.get("finisher_threads", 256))
+                            finisher_threads=sort_tuning.get("finisher_threads", 256),
+                            cluster_sort=sort_tuning.get("cluster_sort", -1))
         loop_info = {"autotuned": False}
     loop_tuning = dict(ks.ksort_get_tuning(ks.F32), **loop_info)
     bounds = [(int(off[r]), int(off[r + 1])) for r in range(len(lengths))]
@@ -844,7 +847,8 @@ def run_batched(ks, args, peak, peak_src):
                         tile_shape=sort_tuning["tile_shape"],
                         wave_levels=sort_tuning.get("wave_levels", -1),
                         finish_in_tiles=sort_tuning.get("finish_in_tiles", -1),
-                            finisher_threads=sort_tuning.get("finisher_threads", 256))
+                            finisher_threads=sort_tuning.get("finisher_threads", 256),
+                            cluster_sort=sort_tuning.get("cluster_sort", -1))
     return {"arrays": len(lengths), "total_keys": total,
             "graph_batched_ms": round(t_batched, 3),
             "graph_batched_runs_ms": [round(x, 3) for x in batched_runs],
@@ -881,7 +885,8 @@ def run_serving(ks, count: int, tuning: dict):
                             tile_shape=tuning["tile_shape"],
                             wave_levels=tuning.get("wave_levels", -1),
                             finish_in_tiles=tuning.get("finish_in_tiles", -1),
-                            finisher_threads=tuning.get("finisher_threads", 256))
+                            finisher_threads=tuning.get("finisher_threads", 256),
+                            cluster_sort=-1)
     cap = serving.measure_capacity()
     torch.cuda.empty_cache()
     srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
@@ -918,7 +923,7 @@ def run_serving(ks, count: int, tuning: dict):
                 "mismatches": mismatches, "check_s": round(time.perf_counter() - t0, 2),
                 "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning.get(k) for k in
                                                            ("cutoff", "ctas_per_sm", "tile_shape", "wave_levels",
-                                                            "finish_in_tiles", "finisher_threads")},
+                                                            "finish_in_tiles", "finisher_threads", "cluster_sort")},
                 "latency": "arrival -> completion event of the request's batch, which follows "
                            "the batch's host-to-device copy, sort and device-to-host copy",
                 "admission": "FIFO batches into a first-fit HBM arena sized from free memory; "

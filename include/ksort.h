@@ -231,6 +231,13 @@ KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t ma
  *   finisher_threads: threads of a shared-memory finisher CTA: 256 (the default), 512
  *                  or 1024. More threads finish one sub-array sooner (fewer CTAs fit an
  *                  SM), which shortens sorts whose finisher is one round of sub-arrays.
+ *   cluster_sort:  ksort_sort of one array that fits the shared memory of one thread-block
+ *                  cluster (16 CTAs, else 8; about 390K 4-byte or 190K 8-byte keys) and
+ *                  has fewer than 512 * (cutoff + 1) keys (cutoff >= 64): 1 = its levels
+ *                  above the cutoff
+ *                  run in that cluster, all sub-arrays of a level at once, exchanging keys
+ *                  through distributed shared memory (one launch, then the finisher);
+ *                  -1 = off (the default): the work queue.
  * A workspace reserved for one tuning serves any cutoff and finisher setting. */
 typedef struct {
     int32_t cutoff;
@@ -243,6 +250,7 @@ typedef struct {
     int32_t sort_reserve;
     int32_t finish_in_tiles;
     int32_t finisher_threads;
+    int32_t cluster_sort;
 } ksort_tuning_t;
 KSORT_API ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *tuning);
 KSORT_API ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out);
@@ -279,6 +287,13 @@ KSORT_API ksort_status_t ksort_partition_shape(ksort_dtype_t dtype, int32_t form
                                                int32_t *threads, int32_t *tile_keys,
                                                int32_t *ctas_per_sm);
 
+/* Cluster form of ksort_sort (tuning cluster_sort) on the current device: the CTAs of
+ * its thread-block cluster (16, else 8; 0 when no cluster of 1024-thread CTAs can run) and
+ * the most keys of `dtype` it holds. Arrays above that, or of 512 * (cutoff + 1) keys or
+ * more, take the work queue. */
+KSORT_API ksort_status_t ksort_cluster_shape(ksort_dtype_t dtype, int32_t *cluster_ctas,
+                                             int64_t *max_keys);
+
 /* Failure-path check: runs one device-side wait, of the kind the partition's look-back
  * uses, on a flag that nothing ever sets. The wait gives up after limit_ms (1..60000),
  * records KSORT_ERR_TIMEOUT in the stream's workspace and returns; the next
@@ -298,8 +313,12 @@ KSORT_API ksort_status_t ksort_selftest_noalloc_timeout(int32_t limit_ms, int64_
  * for tickets < `tickets`: %globaltimer stamps (ns) of [0] ticket claimed, [1] ticket
  * issued, [2] keys loaded and counted, [3] look-back done, [4] written, [5] first
  * look-back window read (0 for tile 0), [6] completed; [7] = CTA index
- * | look-back windows << 20 | look-back polls << 40. The caller owns the buffer
- * (device memory); pass NULL / 0 to stop. Costs a little time. */
+ * | look-back windows << 20 | look-back polls << 40. In the cluster form (tuning
+ * cluster_sort) entry k * 8 + j is level k instead: %globaltimer stamps of [0] level
+ * start, [1] counts scanned, [2] counts of every CTA ready, [3] prefixes read,
+ * [4] keys stored, [5] keys landed, [6] next table built, [7] active sub-arrays (CTA 0).
+ * The caller owns the buffer (device memory); pass NULL / 0 to stop. Costs a little
+ * time. */
 KSORT_API ksort_status_t ksort_debug_trace(uint64_t *trace_dev, int64_t tickets);
 
 /* Static text for a status code. */

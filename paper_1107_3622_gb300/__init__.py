@@ -24,7 +24,8 @@ __all__ = [
     "ksort_get_stats", "ksort_set_phase_timing", "ksort_get_phase_times",
     "ksort_get_phase_history",
     "ksort_set_tuning", "ksort_get_tuning", "ksort_max_cutoff",
-    "ksort_tile_keys", "ksort_tile_shape", "ksort_partition_shape", "ksort_status_string", "ksort_last_cuda_error",
+    "ksort_tile_keys", "ksort_tile_shape", "ksort_partition_shape", "ksort_cluster_shape",
+    "ksort_status_string", "ksort_last_cuda_error",
     "ksort_selftest_wait_timeout", "ksort_selftest_noalloc_timeout", "ksort_debug_trace",
     "partition_", "partition_out", "sort_", "sort_batched_", "dtype_code",
 ]
@@ -65,7 +66,8 @@ class Tuning(ctypes.Structure):
                 ("spin_limit_ms", ctypes.c_int32), ("tile_shape", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("medium_tiles", ctypes.c_int32),
                 ("partition_form", ctypes.c_int32), ("sort_reserve", ctypes.c_int32),
-                ("finish_in_tiles", ctypes.c_int32), ("finisher_threads", ctypes.c_int32)]
+                ("finish_in_tiles", ctypes.c_int32), ("finisher_threads", ctypes.c_int32),
+                ("cluster_sort", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -114,6 +116,8 @@ def load():
             "ksort_partition_shape": (i32, [i32, i32, ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32),
                                             ctypes.POINTER(ctypes.c_int32)]),
+            "ksort_cluster_shape": (i32, [i32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64)]),
             "ksort_status_string": (ctypes.c_char_p, [i32]),
             "ksort_last_cuda_error": (ctypes.c_char_p, []),
             "ksort_selftest_wait_timeout": (i32, [i32, vp]),
@@ -251,16 +255,17 @@ def ksort_get_phase_times(stream=None) -> list:
 def ksort_set_tuning(dtype: int, cutoff: int = 0, ctas_per_sm: int = 0, spin_limit_ms: int = 0,
                      tile_shape: int = 0, wave_levels: int = 0, medium_tiles: int = 0,
                      partition_form: int = 0, sort_reserve: int = 0, finish_in_tiles: int = 0,
-                     finisher_threads: int = 0):
+                     finisher_threads: int = 0, cluster_sort: int = 0):
     """Zero arguments keep their value; ctas_per_sm=-1 restores "as many as fit",
     wave_levels=-1 the automatic level count, medium_tiles=-1 turns whole-item CTAs off,
     partition_form=-1 makes single partitions follow tile_shape instead of the ring,
     sort_reserve=-1 makes sort tile passes take their offsets by look-back,
     finish_in_tiles=W (tile shape 3) lets the tile kernel finish small sub-arrays while
     W or more of its CTAs wait for future tiles; -1 gives the finisher its own launch;
-    finisher_threads (256, 512, 1024) sets the finisher CTA's size."""
+    finisher_threads (256, 512, 1024) sets the finisher CTA's size; cluster_sort=1 runs
+    the upper levels of arrays that fit one thread-block cluster inside it, -1 not."""
     t = Tuning(cutoff, ctas_per_sm, spin_limit_ms, tile_shape, wave_levels, medium_tiles,
-               partition_form, sort_reserve, finish_in_tiles, finisher_threads)
+               partition_form, sort_reserve, finish_in_tiles, finisher_threads, cluster_sort)
     _check(load().ksort_set_tuning(dtype, ctypes.byref(t)), "ksort_set_tuning")
 
 
@@ -271,7 +276,7 @@ def ksort_get_tuning(dtype: int) -> dict:
             "tile_shape": t.tile_shape, "wave_levels": t.wave_levels,
             "medium_tiles": t.medium_tiles, "partition_form": t.partition_form,
             "sort_reserve": t.sort_reserve, "finish_in_tiles": t.finish_in_tiles,
-            "finisher_threads": t.finisher_threads}
+            "finisher_threads": t.finisher_threads, "cluster_sort": t.cluster_sort}
 
 
 def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
@@ -290,6 +295,15 @@ def ksort_partition_shape(dtype: int, form: int) -> tuple[int, int, int]:
     _check(load().ksort_partition_shape(dtype, form, ctypes.byref(nt), ctypes.byref(tk),
                                         ctypes.byref(occ)), "ksort_partition_shape")
     return int(nt.value), int(tk.value), int(occ.value)
+
+
+def ksort_cluster_shape(dtype: int) -> tuple[int, int]:
+    """(CTAs of the cluster form's thread-block cluster, most keys it holds) on the
+    current device; (0, 0) when no cluster can run."""
+    c, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().ksort_cluster_shape(dtype, ctypes.byref(c), ctypes.byref(m)),
+           "ksort_cluster_shape")
+    return int(c.value), int(m.value)
 
 
 def ksort_max_cutoff(dtype: int) -> int:

@@ -2,7 +2,8 @@
 or a single partition), the form of the partition passes (kernel kind and threads x
 keys per thread), the number of level-synchronous levels when that form is the wave
 form, the shared-memory cutoff below which sub-arrays are finished in SMEM, and the
-finisher's CTAs per SM and threads per CTA, and for tile shape 3 whether the tile kernel finishes the small
+finisher's CTAs per SM and threads per CTA, whether a single array that fits one
+thread-block cluster runs its upper levels there, and for tile shape 3 whether the tile kernel finishes the small
 sub-arrays itself (and its park threshold). For a single partition it picks the configuration of the ring
 partition (tile size, slots, CTAs per SM), or the tile shape's own form if that wins.
 
@@ -43,6 +44,7 @@ PARTITION_FORMS = (1, 2, 3, 4, -1)
 FINISH_IN_TILES = (-1, 4, 16, 64)
 FUSED_SHAPE = 3
 FINISHER_THREADS = (256, 512, 1024)
+CLUSTER_SORT = (-1, 1)
 _L2_FLUSH_BYTES = 256 << 20
 _lock = threading.Lock()
 
@@ -112,7 +114,8 @@ def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None) -> dict | None
                      tile_shape=t["tile_shape"], wave_levels=t.get("wave_levels", -1),
                      partition_form=t.get("partition_form", 1),
                      finish_in_tiles=t.get("finish_in_tiles", -1),
-                     finisher_threads=t.get("finisher_threads", 256))
+                     finisher_threads=t.get("finisher_threads", 256),
+                     cluster_sort=t.get("cluster_sort", -1))
     return e
 
 
@@ -208,7 +211,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
             "wave_levels": before.get("wave_levels", -1),
             "partition_form": before.get("partition_form", 1),
             "finish_in_tiles": before.get("finish_in_tiles", -1),
-            "finisher_threads": before.get("finisher_threads", 256)}
+            "finisher_threads": before.get("finisher_threads", 256),
+            "cluster_sort": before.get("cluster_sort", -1)}
     tried = {}
 
     def measure(cfg) -> float:
@@ -217,18 +221,21 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
         if cfg["tile_shape"] != FUSED_SHAPE:
             cfg["finish_in_tiles"] = -1  # only tile shape 3 has the fused finisher
         key = (cfg["tile_shape"], cfg["cutoff"], cfg["ctas_per_sm"], cfg["wave_levels"],
-               cfg["partition_form"], cfg["finish_in_tiles"], cfg["finisher_threads"])
+               cfg["partition_form"], cfg["finish_in_tiles"], cfg["finisher_threads"],
+               cfg["cluster_sort"])
         if key not in tried:
             ksort_set_tuning(dtype, cutoff=cfg["cutoff"], ctas_per_sm=cfg["ctas_per_sm"],
                              tile_shape=cfg["tile_shape"], wave_levels=cfg["wave_levels"],
                              partition_form=cfg["partition_form"],
                              finish_in_tiles=cfg["finish_in_tiles"],
-                             finisher_threads=cfg["finisher_threads"])
+                             finisher_threads=cfg["finisher_threads"],
+                             cluster_sort=cfg["cluster_sort"])
             tried[key] = runner.time(reps)
         return tried[key]
 
     best_ms = measure(best)
-    axes = (("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS),
+    axes = (("cluster_sort", CLUSTER_SORT if kind == "sort" else (-1,)),
+            ("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS),
             ("finish_in_tiles", FINISH_IN_TILES), ("cutoff", cutoffs),
             ("ctas_per_sm", FINISHER_CTAS), ("finisher_threads", FINISHER_THREADS))
     if kind == "partition":
@@ -255,13 +262,15 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
                      tile_shape=best["tile_shape"], wave_levels=best["wave_levels"],
                      partition_form=best["partition_form"],
                      finish_in_tiles=best["finish_in_tiles"],
-                     finisher_threads=best["finisher_threads"])
+                     finisher_threads=best["finisher_threads"],
+                     cluster_sort=best["cluster_sort"])
     if not runner.check_sorted():
         ksort_set_tuning(dtype, cutoff=before["cutoff"], ctas_per_sm=before["ctas_per_sm"] or -1,
                          tile_shape=before["tile_shape"], wave_levels=before.get("wave_levels", -1),
                          partition_form=before.get("partition_form", 1),
                          finish_in_tiles=before.get("finish_in_tiles", -1),
-                         finisher_threads=before.get("finisher_threads", 256))
+                         finisher_threads=before.get("finisher_threads", 256),
+                         cluster_sort=before.get("cluster_sort", -1))
         raise RuntimeError("autotuned configuration produced an unsorted output")
     entry = {"workload": workload_key(kind, dtype, n, lengths), "device": device_key(),
              "library": library_hash(), "tuning": best, "ms": round(best_ms, 4),
@@ -269,7 +278,7 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
              "candidates": [{"tile_shape": k[0], "cutoff": k[1], "ctas_per_sm": k[2],
                              "wave_levels": k[3], "partition_form": k[4],
                              "finish_in_tiles": k[5], "finisher_threads": k[6],
-                             "ms": round(v, 4)}
+                             "cluster_sort": k[7], "ms": round(v, 4)}
                             for k, v in sorted(tried.items())]}
     if use_cache:
         _store(_full_key(kind, dtype, n, lengths), entry)
@@ -279,7 +288,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 def reset(dtype: int):
     """Back to the library defaults (tile shape 1, default cutoff, all finisher CTAs,
     automatic wave levels, ring partition configuration 1, separate finisher launch of
-    256-thread CTAs)."""
+    256-thread CTAs, no cluster form)."""
     default_cutoff = {F32: 4096, F64: 2048, U32: 4096}[dtype]
     ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1, wave_levels=-1,
-                     partition_form=1, finish_in_tiles=-1, finisher_threads=256)
+                     partition_form=1, finish_in_tiles=-1, finisher_threads=256,
+                     cluster_sort=-1)

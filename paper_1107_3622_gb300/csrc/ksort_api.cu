@@ -56,6 +56,8 @@ struct Ops {
   cudaError_t (*ring_partition)(const SortParams &, int, int, cudaStream_t);
   cudaError_t (*fused_occupancy)(int, int *);
   cudaError_t (*tiles_fused)(const SortParams &, int, cudaStream_t);
+  cudaError_t (*cluster_setup)(int *, int *);
+  cudaError_t (*cluster_sort)(const SortParams &, int, int, cudaStream_t);
 };
 
 template <typename K>
@@ -67,7 +69,8 @@ Ops ops_for() {
              &Launcher<K>::wave_occupancy, &Launcher<K>::wave_level, &Launcher<K>::wave_handoff,
              &Launcher<K>::partition_split,
              &Launcher<K>::ring_info,  &Launcher<K>::ring_occupancy, &Launcher<K>::ring_partition,
-             &Launcher<K>::fused_occupancy, &Launcher<K>::tiles_fused};
+             &Launcher<K>::fused_occupancy, &Launcher<K>::tiles_fused,
+             &Launcher<K>::cluster_setup, &Launcher<K>::cluster_sort};
 }
 
 const Ops &ops(ksort_dtype_t dt) {
@@ -88,14 +91,15 @@ struct Tuning {
   int fuse_park;    // tile variant kFusedVariant: finisher inside the tile kernel with this
                     // park threshold; 0: separate finisher launch
   int small_threads;  // finisher CTA: 256, 512 or 1024 threads
+  int cluster;        // single arrays that fit: upper levels in a thread-block cluster
 };
 
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256},
-                      {2048, 0, 2000, 0, 0, 0, 1, 1, 0, 256},
-                      {4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256, 0},
+                      {2048, 0, 2000, 0, 0, 0, 1, 1, 0, 256, 0},
+                      {4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256, 0}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {
@@ -320,6 +324,22 @@ ksort_status_t full_grids(ksort_dtype_t dt, int dev, const Tuning &tu, Grids *g)
   if (tu.ctas_per_sm > 0) small_occ = std::min(small_occ, tu.ctas_per_sm);
   g->tiles = sms * occ.first;
   g->smalls = sms * small_occ;
+  return KSORT_OK;
+}
+
+// (device, dtype) -> (cluster size, largest slice) of the cluster kernel; size 0: none
+std::map<std::pair<int, int>, std::pair<int, int>> g_cluster;
+
+ksort_status_t cluster_setup(ksort_dtype_t dt, int dev, int *csize, int *max_sl) {
+  auto key = std::make_pair(dev, (int)dt);
+  auto it = g_cluster.find(key);
+  if (it == g_cluster.end()) {
+    std::pair<int, int> v{0, 0};
+    KS_CUDA(ops(dt).cluster_setup(&v.first, &v.second));
+    it = g_cluster.emplace(key, v).first;
+  }
+  *csize = it->second.first;
+  *max_sl = it->second.second;
   return KSORT_OK;
 }
 
@@ -603,6 +623,25 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     KS_CUDA(pm.mark());
     ws->launches = 2ull * (unsigned long long)levels + 4ull;
     return KSORT_OK;
+  }
+  if (tu.cluster && !offsets && total > tu.cutoff && tu.cutoff >= 64 &&
+      total < (long long)kClusterMaxSegs * (tu.cutoff + 1)) {
+    // the upper levels in one thread-block cluster, when the array fits its shared memory
+    int csize = 0, max_sl = 0;
+    if ((st = cluster_setup(dt, dev, &csize, &max_sl)) != KSORT_OK) return st;
+    const long long sl = ((total + csize - 1) / std::max(csize, 1) + 3) / 4 * 4;
+    if (csize > 0 && sl <= max_sl) {
+      PhaseMarks pm;
+      if ((st = phase_begin(dev, s, &pm)) != KSORT_OK) return st;
+      KS_CUDA(pm.mark());
+      KS_CUDA(pm.mark());  // no seed launch: the cluster kernel starts the generation
+      KS_CUDA(ops(dt).cluster_sort(p, csize, (int)sl, s));
+      KS_CUDA(pm.mark());
+      KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+      KS_CUDA(pm.mark());
+      ws->launches = 2;
+      return KSORT_OK;
+    }
   }
   if (tu.fuse_park > 0 && tu.variant == kFusedVariant && (offsets || total > tu.cutoff)) {
     // the tile kernel finishes the small items too: while enough of its CTAs already
@@ -1004,6 +1043,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->finisher_threads != 0 && t->finisher_threads != 256 && t->finisher_threads != 512 &&
       t->finisher_threads != 1024)
     return KSORT_ERR_INVALID_ARG;
+  if (t->cluster_sort < -1 || t->cluster_sort > 1) return KSORT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
   Tuning &g = g_tuning[dtype];
   if (t->cutoff) g.cutoff = t->cutoff;
@@ -1016,6 +1056,7 @@ ksort_status_t ksort_set_tuning(ksort_dtype_t dtype, const ksort_tuning_t *t) {
   if (t->sort_reserve) g.reserve = t->sort_reserve > 0 ? 1 : 0;
   if (t->finish_in_tiles) g.fuse_park = t->finish_in_tiles < 0 ? 0 : t->finish_in_tiles;
   if (t->finisher_threads) g.small_threads = t->finisher_threads;
+  if (t->cluster_sort) g.cluster = t->cluster_sort > 0 ? 1 : 0;
   return KSORT_OK;
 }
 
@@ -1034,6 +1075,7 @@ ksort_status_t ksort_get_tuning(ksort_dtype_t dtype, ksort_tuning_t *out) {
   out->sort_reserve = g.reserve ? 1 : -1;
   out->finish_in_tiles = g.fuse_park ? g.fuse_park : -1;
   out->finisher_threads = g.small_threads;
+  out->cluster_sort = g.cluster ? 1 : -1;
   return KSORT_OK;
 }
 
@@ -1062,6 +1104,20 @@ ksort_status_t ksort_selftest_wait_timeout(int32_t limit_ms, ksort_stream_t stre
   selftest_wait_kernel<<<1, 32, 0, s>>>(ws->lb, ws->ctl,
                                         (unsigned long long)limit_ms * 1000000ull);
   KS_CUDA(cudaGetLastError());
+  return KSORT_OK;
+}
+
+ksort_status_t ksort_cluster_shape(ksort_dtype_t dtype, int32_t *cluster_ctas, int64_t *max_keys) {
+  if (!dtype_ok(dtype)) return KSORT_ERR_UNSUPPORTED_DTYPE;
+  if (!cluster_ctas || !max_keys) return KSORT_ERR_INVALID_ARG;
+  int dev = 0;
+  ksort_status_t st = current_device(&dev);
+  if (st != KSORT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_mu);
+  int csize = 0, max_sl = 0;
+  if ((st = cluster_setup(dtype, dev, &csize, &max_sl)) != KSORT_OK) return st;
+  *cluster_ctas = csize;
+  *max_keys = (int64_t)csize * max_sl;
   return KSORT_OK;
 }
 

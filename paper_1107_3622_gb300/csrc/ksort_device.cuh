@@ -1529,12 +1529,13 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       G += b;
     }
     unsigned long long *lb = p.lb + it.lb;
+    unsigned long long resv = 0;
     if (tid == 0) {
       if (p.reserve) {
         // the tile's ranges at once: one add of (>= << 32 | less) to the item's counter
-        // gives the less and >= keys of the tiles that took theirs before
-        sh.E = atomicAdd(&p.ictl[h].less, ((unsigned long long)G << 32) | L);
-        sh.abort = 0;
+        // gives the less and >= keys of the tiles that took theirs before; the result is
+        // first used after the scatter, so its round trip overlaps it
+        resv = atomicAdd(&p.ictl[h].less, ((unsigned long long)G << 32) | L);
       } else {
         st_relaxed(&lb[t], lb_pack(epoch, t == 0, L));  // aggregate (inclusive: tile 0)
       }
@@ -1568,6 +1569,10 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
       }
     }
     scatter_keys<K, IPT>(sout, x, lessbits, gebits, wlx, L + wgx, incl - mine);
+    if (tid == 0 && p.reserve) {
+      sh.E = resv;
+      sh.abort = 0;
+    }
     __syncthreads();
     const unsigned long long E = sh.E;
     if (sh.abort) break;
@@ -3300,6 +3305,26 @@ __global__ void __launch_bounds__(NT) small_kernel(SortParams p) {
   }
 }
 
+// One thread, at the start of a sort: a new generation (which retires every tagged
+// entry of earlier sorts) and cleared dispatch counters and statistics. Returns it.
+__device__ __forceinline__ unsigned start_generation(Control *ctl) {
+  unsigned ep = ctl->epoch + 1u;
+  if (ep == 0u || ep >= kMaxEpoch) ep = 1u;
+  ctl->epoch = ep;
+  ctl->pushed = 0;
+  ctl->large_pushed = ctl->large_completed = 0;
+  ctl->tq_head = 0;
+  ctl->sq_head = ctl->sq_tail = 0;
+  ctl->lb_used = 0;
+  ctl->abort = 0;
+  ctl->large_items = ctl->large_keys = ctl->tiles = 0;
+  ctl->small_items = ctl->small_keys = 0;
+  ctl->smem_levels = ctl->lookback_steps = 0;
+  ctl->wave_ctr[0] = ctl->wave_ctr[1] = 0;
+  ctl->wave_fin = 0;
+  return ep;
+}
+
 // Wave form: a root above the cutoff goes on the level-0 list (true), else false.
 __device__ __forceinline__ bool seed_wave_root(const SortParams &p, long long b, long long e) {
   if (!p.wave || e - b <= p.cutoff || (p.root_flags & kItemPartitionOnly)) return false;
@@ -3324,23 +3349,7 @@ __global__ void seed_kernel(SortParams p) {
   __shared__ unsigned epoch_sh;
   Control *ctl = p.ctl;
   grid_dep_launch();  // the tile kernel may start launching; it waits for this one
-  if (threadIdx.x == 0) {
-    unsigned ep = ctl->epoch + 1u;
-    if (ep == 0u || ep >= kMaxEpoch) ep = 1u;
-    ctl->epoch = ep;
-    ctl->pushed = 0;
-    ctl->large_pushed = ctl->large_completed = 0;
-    ctl->tq_head = 0;
-    ctl->sq_head = ctl->sq_tail = 0;
-    ctl->lb_used = 0;
-    ctl->abort = 0;
-    ctl->large_items = ctl->large_keys = ctl->tiles = 0;
-    ctl->small_items = ctl->small_keys = 0;
-    ctl->smem_levels = ctl->lookback_steps = 0;
-    ctl->wave_ctr[0] = ctl->wave_ctr[1] = 0;
-    ctl->wave_fin = 0;
-    epoch_sh = ep;
-  }
+  if (threadIdx.x == 0) epoch_sh = start_generation(ctl);
   __syncthreads();
   const unsigned epoch = epoch_sh;
   if (!p.offsets) {

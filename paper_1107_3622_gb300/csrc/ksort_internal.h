@@ -145,6 +145,9 @@ constexpr int kWaveMaxGrid = 4096;  // CTAs of one level pass (two counts each)
 constexpr int kTileVariants = kTileForms * kTileShapes;
 // The tile variant whose CTAs can also finish small items (queue form, 256 threads).
 constexpr int kFusedVariant = 2;
+// Cluster form: most sub-arrays above the cutoff that one level can hold (the host
+// takes the cluster form only for arrays of fewer than this many times cutoff + 1 keys).
+constexpr int kClusterMaxSegs = 512;
 // Threads of a finisher CTA: 256 (the default), 512 or 1024.
 constexpr int small_threads_of(int nt) { return nt == 1024 || nt == 512 ? nt : 256; }
 
@@ -175,6 +178,10 @@ struct Launcher {
   static cudaError_t seed(const SortParams &p, int variant, cudaStream_t s);
   static cudaError_t tiles(const SortParams &p, int variant, int grid, cudaStream_t s);
   static cudaError_t smalls(const SortParams &p, int grid, cudaStream_t s);
+  // the upper levels of one array in a thread-block cluster (cluster_kernel): the
+  // cluster size that can run (0: none) and the largest slice per CTA; one launch
+  static cudaError_t cluster_setup(int *csize, int *max_sl);
+  static cudaError_t cluster_sort(const SortParams &p, int csize, int sl, cudaStream_t s);
   // tile_kernel in tile variant kFusedVariant with the finisher inside (no smalls launch)
   static cudaError_t fused_occupancy(int cutoff, int *ctas);
   static cudaError_t tiles_fused(const SortParams &p, int grid, cudaStream_t s);

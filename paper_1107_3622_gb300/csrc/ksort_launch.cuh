@@ -7,6 +7,7 @@
 #include "ksort_device.cuh"
 #include "ksort_part_ring.cuh"
 #include "ksort_tile_ring.cuh"
+#include "ksort_cluster.cuh"
 
 namespace ksort {
 
@@ -330,6 +331,78 @@ cudaError_t Launcher<K>::ring_partition(const SortParams &p, int cfg, int grid, 
     if (e != cudaSuccess) return e;
     return launch_after(fn, grid, C::NT, C::SMEM, p, st);
   });
+}
+
+// ------------------------------------------------------------------ cluster form
+// Largest slice the cluster kernel's dynamic shared memory holds (two buffers), and the
+// largest cluster (16, else 8 CTAs of one GPC) that can run: *csize = 0 when none can.
+template <typename K>
+cudaError_t Launcher<K>::cluster_setup(int *csize, int *max_sl) {
+  auto fn = dev::cluster_kernel<K>;
+  *csize = 0;
+  *max_sl = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+      cudaSuccess)
+    return e;
+  const long long dyn = (long long)optin - (long long)fa.sharedSizeBytes;
+  // chunks are rounded up to an odd length, so at most kClusterMaxChunk - 1 keys each
+  int sl = (int)std::min<long long>(dyn / (2 * (long long)sizeof(K)),
+                                    (long long)(dev::kClusterMaxChunk - 1) * dev::kClusterThreads);
+  sl &= ~3;
+  if (sl < 4) return cudaSuccess;
+  const size_t smem = (size_t)2 * sl * sizeof(K);
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+      cudaSuccess)
+    return e;
+  for (int c : {16, 8}) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)c);
+    cfg.blockDim = dim3((unsigned)dev::kClusterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, fn, &cfg) == cudaSuccess && num >= 1) {
+      *csize = c;
+      *max_sl = sl;
+      return cudaSuccess;
+    }
+    (void)cudaGetLastError();  // this size cannot run: try the next
+  }
+  return cudaSuccess;
+}
+
+template <typename K>
+cudaError_t Launcher<K>::cluster_sort(const SortParams &p, int csize, int sl, cudaStream_t st) {
+  auto fn = dev::cluster_kernel<K>;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)csize);
+  cfg.blockDim = dim3((unsigned)dev::kClusterThreads);
+  cfg.dynamicSmemBytes = (size_t)2 * sl * sizeof(K);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, fn, p, sl);
 }
 
 // ------------------------------------------------------------------ wave form

@@ -176,6 +176,15 @@ def test_tile_shapes_and_tuning_fields(lib):
             assert ks.ksort_get_tuning(code)["finisher_threads"] == nt
         ks.ksort_set_tuning(code, finisher_threads=before["finisher_threads"])
         assert ks.ksort_get_tuning(code) == before
+        assert before["cluster_sort"] in (-1, 1)
+        for bad in (-2, 2):
+            with pytest.raises(ks.KSortError):
+                ks.ksort_set_tuning(code, cluster_sort=bad)
+        for v in (1, -1):
+            ks.ksort_set_tuning(code, cluster_sort=v)
+            assert ks.ksort_get_tuning(code)["cluster_sort"] == v
+        ks.ksort_set_tuning(code, cluster_sort=before["cluster_sort"])
+        assert ks.ksort_get_tuning(code) == before
         # every ring configuration stages the same bytes per tile for 4- and 8-byte keys
         keyb = 8 if code == ks.F64 else 4
         for form in (1, 2, 3, 4):

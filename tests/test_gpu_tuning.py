@@ -29,7 +29,8 @@ def restore(ks):
         ks.ksort_set_tuning(c, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
                             tile_shape=t["tile_shape"], partition_form=t["partition_form"],
                             sort_reserve=t["sort_reserve"], finish_in_tiles=t["finish_in_tiles"],
-                            finisher_threads=t["finisher_threads"])
+                            finisher_threads=t["finisher_threads"],
+                            cluster_sort=t["cluster_sort"])
 
 
 def _sort(ks, a):
