@@ -210,8 +210,8 @@ KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t ma
  *                  sub-array of 2 .. medium_tiles tile passes is taken by one CTA, which
  *                  counts every tile first and then moves them with the prefixes it
  *                  knows (no look-back); 1 .. 16, -1 = off (the default).
- *   partition_form: single partitions (ksort_partition, ksort_partition_out): 1 .. 4 the
- *                  one-pass ring partition in that configuration (1 = the default, see
+ *   partition_form: single partitions (ksort_partition, ksort_partition_out): 1 .. 6 the
+ *                  one-pass ring partition in that configuration (5 = the default, see
  *                  ksort_partition_shape); -1 = the form that tile_shape names.
  *   sort_reserve:  sorts in tile shapes 1 .. 3 and 10 .. 12: 1 (the default) = each tile
  *                  pass takes its output ranges in its sub-array with one atomic add on
@@ -279,10 +279,13 @@ KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
 KSORT_API ksort_status_t ksort_tile_shape(ksort_dtype_t dtype, int32_t shape, int32_t *threads,
                                           int32_t *keys_per_thread, int32_t *form);
 
-/* Configuration `form` (1 .. 4) of the one-pass ring partition for `dtype`: CTAs of
- * *threads threads (one producer warp, one look-back warp, the rest data warps) that
- * stage tiles of *tile_keys keys, compiled for *ctas_per_sm CTAs per SM. Every
- * configuration moves the same bytes per tile for 4- and 8-byte keys. */
+/* Configuration `form` (1 .. 6) of the one-pass ring partition for `dtype`: CTAs of
+ * *threads threads (one producer warp, the data warps, and in configurations 4 .. 6
+ * two role warps) that stage tiles of *tile_keys keys, compiled for *ctas_per_sm CTAs
+ * per SM. 1 .. 3: the last data warp of a tile takes its output ranges (one atomic add);
+ * 4: two role warps take them by look-back, in tile order; 5, 6: two role warps take them
+ * by the atomic add, so the data warps never wait on it. Every configuration moves the
+ * same bytes per tile for 4- and 8-byte keys. */
 KSORT_API ksort_status_t ksort_partition_shape(ksort_dtype_t dtype, int32_t form,
                                                int32_t *threads, int32_t *tile_keys,
                                                int32_t *ctas_per_sm);

@@ -290,7 +290,7 @@ def ksort_tile_shape(dtype: int, shape: int) -> tuple[int, int, int]:
 
 
 def ksort_partition_shape(dtype: int, form: int) -> tuple[int, int, int]:
-    """(threads, tile keys, CTAs per SM) of ring-partition configuration `form` (1-4)."""
+    """(threads, tile keys, CTAs per SM) of ring-partition configuration `form` (1-6)."""
     nt, tk, occ = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(load().ksort_partition_shape(dtype, form, ctypes.byref(nt), ctypes.byref(tk),
                                         ctypes.byref(occ)), "ksort_partition_shape")

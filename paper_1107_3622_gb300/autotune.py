@@ -39,7 +39,7 @@ WAVE_SHAPES = (10, 11, 12)
 WAVE_LEVELS = (-1, 6, 9, 12, 15, 18)
 FINISHER_CTAS = (-1, 3, 2)
 # single partitions: the ring partition's configurations, or -1 (the tile shape's form)
-PARTITION_FORMS = (1, 2, 3, 4, -1)
+PARTITION_FORMS = (1, 2, 3, 4, 5, 6, -1)
 # tile shape 3: -1 (a separate finisher launch) or the fused finisher's park threshold
 FINISH_IN_TILES = (-1, 4, 16, 64)
 FUSED_SHAPE = 3
@@ -112,7 +112,7 @@ def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None) -> dict | None
     t = e["tuning"]
     ksort_set_tuning(dtype, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
                      tile_shape=t["tile_shape"], wave_levels=t.get("wave_levels", -1),
-                     partition_form=t.get("partition_form", 1),
+                     partition_form=t.get("partition_form", 5),
                      finish_in_tiles=t.get("finish_in_tiles", -1),
                      finisher_threads=t.get("finisher_threads", 256),
                      cluster_sort=t.get("cluster_sort", -1))
@@ -209,7 +209,7 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
     best = {"tile_shape": before["tile_shape"], "cutoff": before["cutoff"],
             "ctas_per_sm": before["ctas_per_sm"] or -1,
             "wave_levels": before.get("wave_levels", -1),
-            "partition_form": before.get("partition_form", 1),
+            "partition_form": before.get("partition_form", 5),
             "finish_in_tiles": before.get("finish_in_tiles", -1),
             "finisher_threads": before.get("finisher_threads", 256),
             "cluster_sort": before.get("cluster_sort", -1)}
@@ -267,7 +267,7 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
     if not runner.check_sorted():
         ksort_set_tuning(dtype, cutoff=before["cutoff"], ctas_per_sm=before["ctas_per_sm"] or -1,
                          tile_shape=before["tile_shape"], wave_levels=before.get("wave_levels", -1),
-                         partition_form=before.get("partition_form", 1),
+                         partition_form=before.get("partition_form", 5),
                          finish_in_tiles=before.get("finish_in_tiles", -1),
                          finisher_threads=before.get("finisher_threads", 256),
                          cluster_sort=before.get("cluster_sort", -1))
@@ -287,9 +287,9 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 
 def reset(dtype: int):
     """Back to the library defaults (tile shape 1, default cutoff, all finisher CTAs,
-    automatic wave levels, ring partition configuration 1, separate finisher launch of
+    automatic wave levels, ring partition configuration 5, separate finisher launch of
     256-thread CTAs, no cluster form)."""
     default_cutoff = {F32: 4096, F64: 2048, U32: 4096}[dtype]
     ksort_set_tuning(dtype, cutoff=default_cutoff, ctas_per_sm=-1, tile_shape=1, wave_levels=-1,
-                     partition_form=1, finish_in_tiles=-1, finisher_threads=256,
+                     partition_form=5, finish_in_tiles=-1, finisher_threads=256,
                      cluster_sort=-1)

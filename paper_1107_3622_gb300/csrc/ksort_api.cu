@@ -97,9 +97,9 @@ struct Tuning {
 std::mutex g_mu;
 unsigned long long *g_trace = nullptr;  // diagnostics: per-ticket timestamps
 long long g_trace_cap = 0;
-Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256, 0},
-                      {2048, 0, 2000, 0, 0, 0, 1, 1, 0, 256, 0},
-                      {4096, 0, 2000, 0, 0, 0, 1, 1, 0, 256, 0}};
+Tuning g_tuning[3] = {{4096, 0, 2000, 0, 0, 0, 5, 1, 0, 256, 0},
+                      {2048, 0, 2000, 0, 0, 0, 5, 1, 0, 256, 0},
+                      {4096, 0, 2000, 0, 0, 0, 5, 1, 0, 256, 0}};
 
 // ------------------------------------------------------------------ workspaces
 struct Workspace {

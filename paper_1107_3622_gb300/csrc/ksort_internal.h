@@ -160,7 +160,7 @@ struct KernelInfo {
 };
 
 // One compiled configuration of the ring partition (part_ring_kernel).
-constexpr int kRingConfigs = 4;
+constexpr int kRingConfigs = 6;
 struct RingInfo {
   int block;        // threads per CTA (producer warp, look-back warp, data warps)
   int tile_keys;    // keys per tile

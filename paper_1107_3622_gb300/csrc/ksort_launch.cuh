@@ -282,6 +282,12 @@ template <typename K> struct RingOf<K, 3> {  // reservation: 32 KiB tiles, 6 slo
 template <typename K> struct RingOf<K, 4> {  // ordered: 16 KiB tiles, 6 slots, 2 CTAs per SM, 2 look-back warps
   using Cfg = dev::RingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 12, 2, 3>;
 };
+template <typename K> struct RingOf<K, 5> {  // reservation by 2 role warps: 16 KiB tiles, 6 slots, 2 CTAs per SM
+  using Cfg = dev::RingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 12, 2, 3, true>;
+};
+template <typename K> struct RingOf<K, 6> {  // reservation by 2 role warps: 8 KiB tiles, 8 slots, 3 CTAs per SM
+  using Cfg = dev::RingCfg<K, 8, 32 / (int)sizeof(K), 8, 3, 10, 2, 3, true>;
+};
 
 template <typename K, typename F>
 decltype(auto) with_ring(int c, F &&f) {
@@ -289,13 +295,15 @@ decltype(auto) with_ring(int c, F &&f) {
     case 2: return f(typename RingOf<K, 2>::Cfg{});
     case 3: return f(typename RingOf<K, 3>::Cfg{});
     case 4: return f(typename RingOf<K, 4>::Cfg{});
+    case 5: return f(typename RingOf<K, 5>::Cfg{});
+    case 6: return f(typename RingOf<K, 6>::Cfg{});
     default: return f(typename RingOf<K, 1>::Cfg{});
   }
 }
 
 template <typename K, typename C>
 cudaError_t ring_kernel_of(void (**fn)(SortParams)) {
-  *fn = dev::part_ring_kernel<K, C::NDW, C::IPT, C::S, C::MINB, C::PER, C::NLB, C::DEPTH>;
+  *fn = dev::part_ring_kernel<K, C::NDW, C::IPT, C::S, C::MINB, C::PER, C::NLB, C::DEPTH, C::RESV>;
   cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::SMEM);
   if (e != cudaSuccess) return e;

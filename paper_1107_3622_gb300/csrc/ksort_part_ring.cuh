@@ -53,9 +53,15 @@ namespace dev {
 // look-back warps (0: the reservation form), and at most DEPTH tiles of a CTA loading or
 // waiting to be compacted (more bytes in flight than the memory system needs only queue
 // up in it; the other slots hold compacted tiles until they are written out).
-template <typename K, int NDW_, int IPT_, int S_, int MINB_, int PER_, int NLB_, int DEPTH_>
+template <typename K, int NDW_, int IPT_, int S_, int MINB_, int PER_, int NLB_, int DEPTH_,
+          bool RESV_ = false>
 struct RingCfg {
   static constexpr int NDW = NDW_, IPT = IPT_, S = S_, MINB = MINB_, PER = PER_, NLB = NLB_;
+  // RESV: the NLB role warps take the tiles' output ranges by reservation (one 64-bit
+  // atomic add per tile, the role warps taking tiles in turn) instead of by look-back, so
+  // the data warps never wait on a global round trip
+  static constexpr bool RESV = RESV_;
+  static_assert(!RESV_ || NLB_ > 0, "reservation by role warps needs role warps");
   static constexpr int DEPTH = DEPTH_ < S_ ? DEPTH_ : S_;
   static constexpr int WT = 32 * IPT;    // keys of a warp sub-tile
   static constexpr int TILE = NDW * WT;  // keys of a tile
@@ -275,9 +281,10 @@ __device__ __forceinline__ void ring_compact(K *reg, K key, int a, int b, unsign
 // (A fixed first tile per CTA would save the first claim, but then a CTA's later tiles
 // would wait for the first tiles of CTAs with higher indices, which another kernel on
 // the GPU can keep from starting.)
-template <typename K, int NDW, int IPT, int S, int MINB, int PER, int NLB, int DEPTH_>
+template <typename K, int NDW, int IPT, int S, int MINB, int PER, int NLB, int DEPTH_,
+          bool RESV = false>
 __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(SortParams p) {
-  using C = RingCfg<K, NDW, IPT, S, MINB, PER, NLB, DEPTH_>;
+  using C = RingCfg<K, NDW, IPT, S, MINB, PER, NLB, DEPTH_, RESV>;
   constexpr int DEPTH = C::DEPTH;
   constexpr int WT = C::WT, TILE = C::TILE, R = C::R;
   constexpr int VEC = Vec<K>::N;
@@ -369,9 +376,65 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
       }
     }
     __syncwarp();
+  } else if (NLB > 0 && warp <= NLB && RESV) {
+    // ---------------------------------------------------------------- reservation
+    if constexpr (RESV) {
+    volatile int *const end_at = &sh.end_at;
+    for (int i = warp - 1;; i += NLB) {
+      __syncwarp();  // one decision for the whole warp (see the look-back loop)
+      if (__any_sync(kFull, i >= *end_at)) break;
+      const int s = i % S;
+      int st = ring_wait_warp(&sh.counted[s], (unsigned)(i / S) & 1u, limit, stp, end_at, i);
+      if (st) {
+        if (st == 1 && lane == 0) ring_fail(ctl, stop, epoch, kDevTimeout, 0x1300000000ull | (unsigned)i);
+        break;
+      }
+      const long long t = sh.tix[i % R];
+      if (t < 0) break;
+      // the data warps' counts: exclusive prefixes of (less, >=) over the warps
+      const unsigned c = lane < NDW ? sh.cnt[s][lane] : 0u;
+      const unsigned Lw = c & 0xffffu, Gw = (c >> 16) - Lw;
+      const unsigned v = Lw | (Gw << 16);
+      unsigned inc = v;
+#pragma unroll
+      for (int d = 1; d < NDW; d <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += u;
+      }
+      const unsigned tot = __shfl_sync(kFull, inc, NDW - 1);
+      const unsigned ex = inc - v;
+      const long long A = tot & 0xffffu, GT = tot >> 16;
+      // the tile's ranges at once: the (>=, less) keys of the tiles that reserved before
+      unsigned long long pre = 0;
+      if (lane == 0) pre = atomicAdd(&ctl->ring_resv, ((unsigned long long)GT << 32) | (unsigned long long)A);
+      pre = __shfl_sync(kFull, pre, 0);
+      const long long PL = (long long)(pre & 0xffffffffull), PG = (long long)(pre >> 32);
+      bool ok = PL + PG + A + GT <= n - 1;
+      if (lane < NDW) {
+        const long long lb = PL + (long long)(ex & 0xffffu);
+        const long long gb = n - PG - GT + (long long)(ex >> 16);
+        ok = ok && lb >= 0 && lb + Lw <= n && gb >= 1 && gb + Gw <= n;
+        sh.lbase[s][lane] = (int)lb;
+        sh.gbase[s][lane] = (int)gb;
+      }
+      if (!__all_sync(kFull, ok)) {  // never released for writing
+        if (lane == 0) ring_fail(ctl, stop, epoch, kDevInternal, 0x1400000000ull | (unsigned)t);
+        break;
+      }
+      if (lane == 0) {
+        if (PL + PG + A + GT == n - 1) {  // every key placed: Step 4
+          dst[PL + A] = key;
+          if (p.key_index) *p.key_index = PL + A;
+        }
+        trace_mark(p, (unsigned long long)t, 3);  // offsets known
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sh.ready[s]);
+    }
+    }
   } else if (NLB > 0 && warp <= NLB) {
     // ---------------------------------------------------------------- look-back
-    if constexpr (NLB > 0) {
+    if constexpr (NLB > 0 && !RESV) {
     volatile int *const end_at = &sh.end_at;
     volatile unsigned long long *const chain = &sh.chain;
     unsigned windows = 0;
@@ -522,8 +585,8 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
       if (lane == 0) {
         sh.cnt[s][dw] = ((L + G) << 16) | L;
         __threadfence_block();  // the counts before the tile's completion count
-        const unsigned old = atomicAdd(&sh.acc[s], (1u << 20) + L);
-        if ((old >> 20) == (unsigned)NDW - 1u) {  // the last warp of the tile
+        const unsigned old = RESV ? 0u : atomicAdd(&sh.acc[s], (1u << 20) + L);
+        if (!RESV && (old >> 20) == (unsigned)NDW - 1u) {  // the last warp of the tile
           __threadfence_block();
           sh.acc[s] = 0u;
           if constexpr (NLB > 0) {  // ordered form: publish the tile's aggregate

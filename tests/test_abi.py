@@ -139,8 +139,8 @@ def test_tile_shapes_and_tuning_fields(lib):
         assert ks.ksort_get_tuning(code) == before
     for code in (ks.F32, ks.F64, ks.U32):
         before = ks.ksort_get_tuning(code)
-        assert before["partition_form"] in (-1, 1, 2, 3, 4)
-        for bad in (-2, 5):
+        assert before["partition_form"] in (-1, 1, 2, 3, 4, 5, 6)
+        for bad in (-2, 7):
             with pytest.raises(ks.KSortError):
                 ks.ksort_set_tuning(code, partition_form=bad)
         ks.ksort_set_tuning(code, partition_form=-1)
@@ -187,11 +187,11 @@ def test_tile_shapes_and_tuning_fields(lib):
         assert ks.ksort_get_tuning(code) == before
         # every ring configuration stages the same bytes per tile for 4- and 8-byte keys
         keyb = 8 if code == ks.F64 else 4
-        for form in (1, 2, 3, 4):
+        for form in (1, 2, 3, 4, 5, 6):
             nt, tile, occ = ks.ksort_partition_shape(code, form)
             assert nt % 32 == 0 and nt >= 96 and occ >= 1
             assert tile * keyb == ks.ksort_partition_shape(ks.F32, form)[1] * 4
-        for bad in (0, 5):
+        for bad in (0, 7):
             with pytest.raises(ks.KSortError):
                 ks.ksort_partition_shape(code, bad)
     # shared-memory staging of two cutoff-sized buffers must fit a CTA (227 KB)

@@ -16,7 +16,7 @@ import ksort_inputs as gen
 pytestmark = pytest.mark.gpu
 
 DTYPES = {"f32": 0, "f64": 1, "u32": 2}
-FORMS = [1, 2, 3, 4]
+FORMS = [1, 2, 3, 4, 5, 6]
 
 
 @pytest.fixture(scope="module")
@@ -90,7 +90,7 @@ def test_ring_sizes(ref, ks, restore, dtype, form):
 def test_ring_stress_patterns(ref, ks, restore, dtype, pattern):
     """Sorted input sends every key right of the first, reverse input every key left;
     16 distinct values put long runs equal to the key on the right side (Step 3)."""
-    for form in (1, 4):
+    for form in (1, 4, 5):
         ks.ksort_set_tuning(DTYPES[dtype], partition_form=form)
         for n in (50_000, 2_000_003):
             a = gen.make(pattern, dtype, n, gen.seed_for(7, 20, n % 997))
@@ -170,7 +170,7 @@ def test_ring_graph_replay(ref, ks, restore):
     """Captured once in a CUDA graph (workspace reserved first) and replayed: every
     replay partitions the current input afresh."""
     import torch
-    ks.ksort_set_tuning(0, partition_form=1)
+    ks.ksort_set_tuning(0, partition_form=5)
     n = 2_500_001
     s = torch.cuda.Stream()
     src = torch.empty(n, dtype=torch.float32, device="cuda")
@@ -197,18 +197,21 @@ def test_ring_graph_replay(ref, ks, restore):
 
 def test_ring_full_size(ref, ks, restore):
     """The 5e7-key float32 partition that bench.py times, in the configuration the
-    library defaults to, against the oracle's own partition of the same array."""
+    library defaults to (5) and in configuration 1, against the oracle's own partition
+    of the same array."""
     import torch
-    ks.ksort_set_tuning(0, partition_form=1)
     n = 50_000_000
     a = gen.uniform_f32(gen.seed_for(1, 6, 500), n)
     want = a.copy()
     ri, *_ = ref.partition(want)
     src = to_dev(a)
-    dst = torch.empty_like(src)
-    i = int(ks.partition_out(src, dst).item())
-    assert ks.ksort_get_device_error() == 0
-    check_sides(dst.cpu().numpy(), i, want, ri, a[0])
+    for form in (5, 1):
+        ks.ksort_set_tuning(0, partition_form=form)
+        dst = torch.empty_like(src)
+        i = int(ks.partition_out(src, dst).item())
+        assert ks.ksort_get_device_error() == 0
+        check_sides(dst.cpu().numpy(), i, want, ri, a[0])
+        del dst
 
 
 def test_legacy_forms_still_selectable(ref, ks, restore):
