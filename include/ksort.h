@@ -265,9 +265,9 @@ KSORT_API int32_t ksort_tile_keys(ksort_dtype_t dtype);
  * vector). Three CTA shapes come in four kinds (*form):
  *   0 (shapes 1-3):   every thread loads its keys of a tile straight into registers;
  *   1 (shapes 4-6):   a ring of shared-memory tiles: one warp stages tiles by bulk
- *                     copies, the other warps (threads - 32) compact them in place and
- *                     take each tile's output ranges by reservation, so a CTA keeps
- *                     several tiles in flight and no tile waits for another;
+ *                     copies, the data warps (threads - 64) compact them in place, and
+ *                     one warp takes each tile's output ranges by reservation, so a CTA
+ *                     keeps several tiles in flight and no tile waits for another;
  *   2 (shapes 7-9):   warp roles, with one warp loading tiles by bulk copies, one warp
  *                     running look-backs and completions, and the rest (threads - 64)
  *                     counting, scattering and writing, so consecutive tiles overlap;

@@ -3,20 +3,23 @@
 // tile_ring_kernel, the staged form of the tile passes.
 //
 // Work comes from the same queue as tile_kernel: one ticket per tile pass, issued when
-// the sub-array that owns it is queued. A CTA has two roles:
+// the sub-array that owns it is queued. A CTA has three roles:
 //   producer  (lane 0 of warp 0) claims tickets in order, waits until each is issued,
 //             and stages the tile's keys into the next free slot by one bulk copy, with
 //             at most DEPTH tiles of the CTA loading or waiting to be compacted;
 //   data warps (NDW of them) each classify one warp sub-tile of 32 x IPT keys with
 //             ballots and compact it in place (less keys to the front of the warp's
-//             region, >= keys to its back). The last data warp to finish a tile adds the
-//             tile's (>= count << 32 | less count) to its sub-array's counter; the value
-//             before the add places the tile's runs: less keys after the less keys
+//             region, >= keys to its back), and publish their counts;
+//   reservation warp (warp 1), tile by tile once every data warp has counted it: adds
+//             the tile's (>= count << 32 | less count) to its sub-array's counter; the
+//             value before the add places the tile's runs: less keys after the less keys
 //             already placed, >= keys before the >= keys already placed, from the right
-//             end. Each warp then writes its two runs with 128-bit stores. The last warp
-//             to write a tile counts it done in its sub-array; the one that completes the
-//             sub-array places its key at begin + #{x < key} (Step 4, the counter's final
-//             less count) and queues both sides (Steps 5-6).
+//             end. (When the last data warp did this itself, it fell behind on every
+//             round trip and became the last warp of the next tile too.)
+// Each data warp then writes its two runs with 128-bit stores. The last warp to write a
+// tile counts it done in its sub-array; the one that completes the sub-array places its
+// key at begin + #{x < key} (Step 4, the counter's final less count) and queues both
+// sides (Steps 5-6).
 // No tile waits for another tile, only for its own keys and its ticket; the order of the
 // tiles' runs inside each side follows the order in which tiles finished (only the key
 // index and the two sides' contents are defined). A data warp writes out every tile
@@ -41,7 +44,7 @@ struct TileRingCfg {
   static constexpr int DEPTH = DEPTH_ < S_ ? DEPTH_ : S_;
   static constexpr int WT = 32 * IPT;
   static constexpr int TILE = NDW * WT;
-  static constexpr int NT = (NDW + 1) * 32;
+  static constexpr int NT = (NDW + 2) * 32;  // producer, reservation warp, data warps
   static constexpr size_t SLOT = (size_t)TILE * sizeof(K) + 128;  // + copy_out_v's over-read
   static constexpr size_t SMEM = (size_t)S * SLOT;
   static_assert(TILE < 65536 && (TILE * sizeof(K)) % 128 == 0 && S >= 2, "bad ring shape");
@@ -51,10 +54,10 @@ template <int NDW, int S>
 struct TileRingShared {
   unsigned long long full[S];   // slot holds its tile's keys (copy landed), or the end mark
   unsigned long long empty[S];  // every data warp has written its share out
+  unsigned long long counted[S];  // every data warp has compacted its share (or seen the end)
   unsigned long long ready[S];  // the tile's output ranges are in lbase / gbase
   PipeTile info[S];             // the slot's tile: item, ticket, geometry (h < 0: end mark)
   unsigned cnt[S][NDW];         // per data warp: (valid keys << 16) | less keys
-  unsigned acc[S];              // (data warps done compacting << 20) + less keys
   unsigned wdone[S];            // data warps done writing the tile out
   long long lbase[S][NDW];      // buffer index of each data warp's first less key
   long long gbase[S][NDW];      // buffer index of each data warp's first >= key
@@ -116,7 +119,7 @@ __device__ __forceinline__ void finish_item_warp(const SortParams &p, unsigned e
 }
 
 template <typename K, int NDW, int IPT, int S, int MINB, int DEPTH_>
-__global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortParams p) {
+__global__ void __launch_bounds__((NDW + 2) * 32, MINB) tile_ring_kernel(SortParams p) {
   using C = TileRingCfg<K, NDW, IPT, S, MINB, DEPTH_>;
   constexpr int WT = C::WT, TILE = C::TILE, DEPTH = C::DEPTH;
   extern __shared__ __align__(128) unsigned char tring_smem[];
@@ -140,8 +143,8 @@ __global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortPar
     for (int s = 0; s < S; ++s) {
       mbar_init(&sh.full[s], 1);
       mbar_init(&sh.empty[s], NDW);
+      mbar_init(&sh.counted[s], NDW);
       mbar_init(&sh.ready[s], 1);
-      sh.acc[s] = 0;
       sh.wdone[s] = 0;
     }
     sh.stop = 0;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortPar
         if (i >= S)  // the slot's previous tile must have been written out
           st = ring_wait_one(&sh.empty[s], (unsigned)((i / S) - 1) & 1u, limit, stp);
         if (!st && DEPTH < S && i >= DEPTH)  // tile i - DEPTH must have been compacted
-          st = ring_wait_one(&sh.ready[(i - DEPTH) % S], (unsigned)((i - DEPTH) / S) & 1u,
+          st = ring_wait_one(&sh.counted[(i - DEPTH) % S], (unsigned)((i - DEPTH) / S) & 1u,
                              limit, stp);
         if (st) {
           if (st == 1) fail(kDevTimeout, 0x1300000000ull | (unsigned)i);
@@ -189,9 +192,55 @@ __global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortPar
       }
     }
     __syncwarp();
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- reservation
+    // Tile by tile, once every data warp has compacted its share: the tile's output
+    // ranges in its item by one 64-bit add of (>= << 32 | less) to the item's counter
+    // (the value before it counts the tiles that reserved earlier), then the tile is
+    // released for writing. The data warps never wait on this round trip themselves.
+    for (int i = 0;; ++i) {
+      const int s = i % S;
+      const int st = ring_wait_warp(&sh.counted[s], (unsigned)(i / S) & 1u, limit, stp);
+      if (st) {
+        if (st == 1 && lane == 0) fail(kDevTimeout, 0x1600000000ull | (unsigned)i);
+        break;
+      }
+      const PipeTile &pt = sh.info[s];
+      if (pt.h < 0) break;  // the end mark
+      const unsigned c = lane < NDW ? sh.cnt[s][lane] : 0u;
+      const unsigned Lw = c & 0xffffu, Gw = (c >> 16) - Lw;
+      const unsigned v = Lw | (Gw << 16);
+      unsigned inc = v;
+#pragma unroll
+      for (int d = 1; d < NDW; d <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += u;
+      }
+      const unsigned tot = __shfl_sync(kFull, inc, NDW - 1);
+      const unsigned ex = inc - v;
+      const unsigned Lt = tot & 0xffffu, Gt = tot >> 16;
+      unsigned long long pre = 0;
+      if (lane == 0) pre = atomicAdd(&p.ictl[pt.h].less, ((unsigned long long)Gt << 32) | Lt);
+      pre = __shfl_sync(kFull, pre, 0);
+      const long long PL = (long long)(pre & 0xffffffffull), PG = (long long)(pre >> 32);
+      const long long lb0 = pt.it.begin + PL, gb0 = pt.it.end - PG - (long long)Gt;
+      if (!ranges_ok(pt.it.begin, pt.it.end, lb0, Lt, gb0, Gt)) {
+        if (lane == 0) fail(kDevInternal, 0x1400000000ull | (unsigned)pt.t);  // never released
+        break;
+      }
+      if (lane < NDW) {
+        sh.lbase[s][lane] = lb0 + (long long)(ex & 0xffffu);
+        sh.gbase[s][lane] = gb0 + (long long)(ex >> 16);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        trace_mark(p, pt.k, 3);  // ranges known
+        mbar_arrive(&sh.ready[s]);
+      }
+    }
   } else {
     // ---------------------------------------------------------------- data warps
-    const int dw = warp - 1;
+    const int dw = warp - 2;
     K *const buf0 = static_cast<K *>(p.keys);
     K *const buf1 = static_cast<K *>(p.scratch);
     // this warp's two runs of the CTA's j-th tile go out; the last warp to write a tile
@@ -257,6 +306,8 @@ __global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortPar
         const PipeTile &pt = sh.info[s];
         if (pt.h < 0) {
           end = i;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.counted[s]);  // the reservation warp sees it too
           continue;
         }
         const int e0 = dw * WT;
@@ -269,38 +320,7 @@ __global__ void __launch_bounds__((NDW + 1) * 32, MINB) tile_ring_kernel(SortPar
         __syncwarp();
         if (lane == 0) {
           sh.cnt[s][dw] = ((L + G) << 16) | L;
-          __threadfence_block();
-          const unsigned old = atomicAdd(&sh.acc[s], (1u << 20) + L);
-          if ((old >> 20) == (unsigned)NDW - 1u) {
-            // the last warp of the tile: its ranges in the item, at once
-            __threadfence_block();
-            sh.acc[s] = 0u;
-            unsigned Lt = 0, Gt = 0;
-            long long lw[NDW], gw[NDW];
-#pragma unroll
-            for (int w = 0; w < NDW; ++w) {
-              const unsigned cw = sh.cnt[s][w];
-              lw[w] = Lt;
-              gw[w] = Gt;
-              Lt += cw & 0xffffu;
-              Gt += (cw >> 16) - (cw & 0xffffu);
-            }
-            const unsigned long long pre =
-                atomicAdd(&p.ictl[pt.h].less, ((unsigned long long)Gt << 32) | Lt);
-            const long long PL = (long long)(pre & 0xffffffffull), PG = (long long)(pre >> 32);
-            const long long lb0 = pt.it.begin + PL, gb0 = pt.it.end - PG - (long long)Gt;
-            if (!ranges_ok(pt.it.begin, pt.it.end, lb0, Lt, gb0, Gt)) {
-              fail(kDevInternal, 0x1400000000ull | (unsigned)pt.t);  // never released
-            } else {
-#pragma unroll
-              for (int w = 0; w < NDW; ++w) {
-                sh.lbase[s][w] = lb0 + lw[w];
-                sh.gbase[s][w] = gb0 + gw[w];
-              }
-              trace_mark(p, pt.k, 3);  // ranges known
-              mbar_arrive(&sh.ready[s]);
-            }
-          }
+          mbar_arrive(&sh.counted[s]);  // release: the count before the arrival
         }
         ++i;
         progress = true;

@@ -102,12 +102,12 @@ def test_tile_shapes_and_tuning_fields(lib):
             assert nt % 32 == 0 and ipt % vec == 0 and ipt <= 32
         assert len(set(shapes)) == 12
         assert [fm for _, _, fm in shapes] == [0] * 3 + [1] * 3 + [2] * 3 + [3] * 3
-        # forms 0, 2 and 3 share their CTA shapes; form 1 (the ring) has its own: one
-        # producer warp and data warps
+        # forms 0, 2 and 3 share their CTA shapes; form 1 (the ring) has its own: a
+        # producer warp, a reservation warp and data warps
         assert [s[:2] for s in shapes[:3]] == [s[:2] for s in shapes[6:9]] == \
             [s[:2] for s in shapes[9:]]
         for nt, ipt, _ in shapes[3:6]:
-            assert (nt - 32) % 256 == 0
+            assert (nt - 64) % 256 == 0
         with pytest.raises(ks.KSortError):
             ks.ksort_tile_shape(code, 0)
         with pytest.raises(ks.KSortError):

@@ -56,8 +56,8 @@ def test_tile_shapes_sort_and_partition(ref, ks, restore, dtype, shape):
     ks.ksort_set_tuning(code, tile_shape=shape, partition_form=-1)
     nt, ipt, form = ks.ksort_tile_shape(code, shape)
     # the keys of one tile pass: the data warps' share (warp roles: two warps load and
-    # look back; the ring: one warp loads)
-    tile = (nt - 64 if form == 2 else nt - 32 if form == 1 else nt) * ipt
+    # look back; the ring: one warp loads, one reserves)
+    tile = (nt - 64 if form in (1, 2) else nt) * ipt
     assert ks.ksort_tile_keys(code) == tile
     for n in (tile - 1, tile + 1, 3 * tile + 5, 250_003):
         a = gen.make("uniform", dtype, n, gen.seed_for(6, shape, n % 1009))
