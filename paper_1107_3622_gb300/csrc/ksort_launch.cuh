@@ -285,8 +285,8 @@ template <typename K> struct RingOf<K, 4> {  // ordered: 16 KiB tiles, 6 slots, 
 template <typename K> struct RingOf<K, 5> {  // reservation by 2 role warps: 16 KiB tiles, 6 slots, 2 CTAs per SM
   using Cfg = dev::RingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 12, 2, 3, true>;
 };
-template <typename K> struct RingOf<K, 6> {  // reservation by 2 role warps: 8 KiB tiles, 8 slots, 3 CTAs per SM
-  using Cfg = dev::RingCfg<K, 8, 32 / (int)sizeof(K), 8, 3, 10, 2, 3, true>;
+template <typename K> struct RingOf<K, 6> {  // reservation by 2 role warps: 16 KiB tiles, 6 slots, 2 CTAs per SM, 4 tiles in flight
+  using Cfg = dev::RingCfg<K, 8, 64 / (int)sizeof(K), 6, 2, 12, 2, 4, true>;
 };
 
 template <typename K, typename F>

@@ -307,8 +307,14 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
   const RingStop stp{stop, &ctl->ring_abort, epoch};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const K key = __ldcg(src);  // Step 1: the first element is the key
-  // the first claim is in flight while the barriers are set up
-  unsigned long long tk = threadIdx.x == 0 ? atomicAdd(&ctl->part_ticket, 1ull) : 0ull;
+  // First tile: in the reservation forms no tile waits for another, so CTA b takes
+  // tile b without a claim (later claims count from gridDim.x); the ordered form's tiles
+  // wait for their predecessors, so there every tile is claimed, in the order CTAs run.
+  constexpr bool kStaticFirst = NLB == 0 || RESV;
+  const unsigned long long t_first = kStaticFirst ? (unsigned long long)gridDim.x : 0ull;
+  unsigned long long tk = 0;
+  if (threadIdx.x == 0)
+    tk = kStaticFirst ? (unsigned long long)blockIdx.x : atomicAdd(&ctl->part_ticket, 1ull);
 
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
         if (p.trace && (unsigned long long)t < (unsigned long long)p.trace_cap)
           p.trace[t * kTraceWords + 7] = blockIdx.x | ((unsigned long long)i << 20) |
                                          ((unsigned long long)epoch << 40);
-        tk = atomicAdd(&ctl->part_ticket, 1ull);  // the next claim overlaps this copy
+        tk = t_first + atomicAdd(&ctl->part_ticket, 1ull);  // the next claim overlaps this copy
       }
     }
     __syncwarp();
