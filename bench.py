@@ -506,8 +506,7 @@ def run_ours(args, dist: Dist):
         if "batched" in extras:
             line["batched"] = run_batched(ks, args, peak, peak_src)
         if "serving" in extras and args.serving_requests > 0:
-            bt = line.get("batched", {}).get("batched_tuning") or ks.ksort_get_tuning(ks.F32)
-            line["serving"] = run_serving(ks, args.serving_requests, bt)
+            line["serving"] = run_serving(ks, args.serving_requests, None)
         if "cpu" in extras:
             v, sample, spent = cpu_baseline(min(n, N_KEYS), args.cpu_seconds, None)
             line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1,
@@ -871,15 +870,23 @@ def run_batched(ks, args, peak, peak_src):
             "batched_tuning": batched_tuning, "loop_tuning": loop_tuning}
 
 
-def run_serving(ks, count: int, tuning: dict):
+def run_serving(ks, count: int, tuning: dict | None):
     """Serving configuration: `count` Poisson requests, sizes log-uniform in
     [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys in page-locked host memory,
     copied into an HBM arena at admission and back when sorted; the arena is sized from
     the HBM left free after the slot workspaces. The rate is 0.8 x the server's own
     throughput on a burst of 500 requests of the same mix, / mean keys per request."""
     import torch
-    from paper_1107_3622_gb300 import serving
-    # serving batches take the batched form's tuning, for both 4-byte key types
+    from paper_1107_3622_gb300 import autotune, serving
+    # serving batches (a few arrays of 1e3 .. 1e7 keys) take the autotuner's choice for a
+    # 256-request batch of the serving mix (`tuning`, when given, is applied instead)
+    if tuning is None:
+        mix = serving.poisson_requests(256, 1.0, seed=gen.seed_for(5, 2, 0))
+        lens = np.array([r.n for r in mix], np.int64)
+        while lens.sum() > (1 << 28):
+            lens = lens[:-1]
+        e = autotune.autotune("batched", ks.F32, lengths=lens, reps=3)
+        tuning = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, cached=e["cached"])
     for code in (ks.F32, ks.U32):
         ks.ksort_set_tuning(code, cutoff=tuning["cutoff"], ctas_per_sm=tuning["ctas_per_sm"] or -1,
                             tile_shape=tuning["tile_shape"],
