@@ -221,13 +221,11 @@ KSORT_API ksort_status_t ksort_get_phase_times(ksort_stream_t stream, int32_t ma
  *                  each later sub-array does). -1 = decoupled look-back in tile order
  *                  (the layout depends on the input alone).
  *   finish_in_tiles: sorts in tile shape 3 only: W (1 .. 4096) = the CTAs of the tile
- *                  passes also finish the small sub-arrays (the shared-memory finisher)
- *                  while the tile passes run: a CTA about to take a new tile takes a
- *                  queued small sub-array instead whenever other CTAs already wait for W
- *                  or more tiles of sub-arrays not yet queued, and every CTA finishes the
- *                  remaining small sub-arrays when the tile passes end, so no separate
- *                  finisher launch follows (the finisher phase of the phase times is
- *                  empty); -1 = off (the default): the finisher is its own launch.
+ *                  passes also finish small sub-arrays (the shared-memory finisher) while
+ *                  the tile passes run: a CTA about to take a new tile takes a queued
+ *                  small sub-array instead whenever other CTAs already wait for W or more
+ *                  tiles of sub-arrays not yet queued. The finisher launch then takes the
+ *                  small sub-arrays left; -1 = off (the default).
  *   finisher_threads: threads of a shared-memory finisher CTA: 256 (the default), 512
  *                  or 1024. More threads finish one sub-array sooner (fewer CTAs fit an
  *                  SM), which shortens sorts whose finisher is one round of sub-arrays.

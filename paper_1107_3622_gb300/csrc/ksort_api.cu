@@ -644,9 +644,9 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     }
   }
   if (tu.fuse_park > 0 && tu.variant == kFusedVariant && (offsets || total > tu.cutoff)) {
-    // the tile kernel finishes the small items too: while enough of its CTAs already
-    // wait for tiles of items still to come, the others take small items, and all of
-    // them drain the small list at the end; no finisher launch follows
+    // the tile kernel finishes small items too: while enough of its CTAs already wait
+    // for tiles of items still to come, the others take small items; the finisher
+    // launch that follows takes the rest of the small list
     int focc = 0, sms = 0;
     if ((st = fused_occupancy(dt, tu.cutoff, &focc)) != KSORT_OK) return st;
     if ((st = device_sms(dev, &sms)) != KSORT_OK) return st;
@@ -664,8 +664,9 @@ ksort_status_t sort_impl(ksort_dtype_t dt, void *keys, const int64_t *offsets, i
     KS_CUDA(pm.mark());
     KS_CUDA(ops(dt).tiles_fused(p, (int)grid, s));
     KS_CUDA(pm.mark());
-    KS_CUDA(pm.mark());  // the finisher phase is empty: its work ran inside the tile kernel
-    ws->launches = 2;
+    KS_CUDA(ops(dt).smalls(p, g.smalls, s));
+    KS_CUDA(pm.mark());
+    ws->launches = 3;
     return KSORT_OK;
   }
   PhaseMarks pm;

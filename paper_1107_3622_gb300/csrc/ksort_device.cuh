@@ -1257,11 +1257,10 @@ __device__ __forceinline__ void finish_item(const SortParams &p, unsigned epoch,
 }
 
 // FUSE: the CTAs also finish small items (dynamic shared memory: SmallShared, then the
-// finisher's buffers for p.cutoff keys). A CTA about to
-// claim a ticket takes a queued small item instead while at least p.fuse_park tickets
-// are held beyond the ones issued (CTAs already parked for items still to come), and
-// every CTA drains the small list once the tile passes are over, so no finisher launch
-// follows.
+// finisher's buffers for p.cutoff keys). A CTA about to claim a ticket takes a queued
+// small item instead while at least p.fuse_park tickets are held beyond the ones issued
+// (CTAs already parked for items still to come). The finisher launch that follows takes
+// what is left of the small list.
 template <typename K, int NT, int IPT, bool FUSE>
 __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParams p) {
   constexpr int TILE = NT * IPT;
@@ -1343,16 +1342,7 @@ __global__ void __launch_bounds__(NT, tile_min_blocks(NT)) tile_kernel(SortParam
                                  &st_segs, [] {});
         continue;
       }
-      if (sh.r == 0) {  // the tile passes are over: drain the small list
-        while (true) {
-          if (tid == 0) sh.r = claim_small(p, epoch, &sh.h, &sh.it);
-          __syncthreads();
-          if (sh.r <= 0) break;
-          finish_small_item<K, NT>(p, sh.it, sh.h, buf0, buf1, sm, q, &st_small,
-                                   &st_small_keys, &st_segs, [] {});
-        }
-        break;
-      }
+
     }
     if (sh.r <= 0) break;
     if (sh.it.flags & kItemMedium) {
@@ -1669,6 +1659,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
       : "memory");
   return ok != 0;
 }
+// The same with a suspend-time hint: the thread sleeps until the phase completes or
+// about hint_ns pass, instead of returning after the hardware's own short limit, so an
+// idle warp does not take issue slots from the warps that work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long *bar, unsigned parity,
+                                                    unsigned hint_ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -1760,6 +1765,18 @@ __device__ __forceinline__ bool nbar_or(int id, int count, bool pred) {
 }
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// An arrival that orders nothing: for a barrier whose waiter needs no data from the
+// arriving thread, only the fact that its earlier reads are done (whose results the
+// thread has already used).
+__device__ __forceinline__ void mbar_arrive_relaxed(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.relaxed.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// `count` arrivals at once.
+__device__ __forceinline__ void mbar_arrive_n(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
 }
 // Waits for phase `parity` of `bar`; gives up (false) after limit_ns or once the sort is
 // aborted.

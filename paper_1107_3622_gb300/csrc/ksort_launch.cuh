@@ -3,6 +3,9 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "ksort_device.cuh"
 #include "ksort_part_ring.cuh"
@@ -10,6 +13,30 @@
 #include "ksort_cluster.cuh"
 
 namespace ksort {
+
+// Allows `fn` `smem` bytes of dynamic shared memory on the current device and, with
+// `carve`, asks for the largest shared-memory carveout. The runtime keeps function
+// attributes per device, so the driver calls are made only when the function does not
+// yet have this limit there (one launch otherwise pays them every time).
+inline cudaError_t allow_smem(void (*fn)(SortParams), size_t smem, bool carve) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  const std::pair<const void *, int> key(reinterpret_cast<const void *>(fn), dev);
+  auto it = done.find(key);
+  if (it != done.end() && it->second == smem) return cudaSuccess;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  if (carve && (e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+    return e;
+  done[key] = smem;
+  return cudaSuccess;
+}
 
 // Compiled tile shapes (threads x keys per thread) of the tile passes, picked at run
 // time by the tuning's tile shape; every shape moves 128-bit vectors. Variant 0 is the
@@ -87,11 +114,7 @@ cudaError_t tile_kernel_of(void (**fn)(SortParams)) {
       using R = typename S::Ring;
       *fn = dev::tile_ring_kernel<K, R::NDW, R::IPT, R::S, R::MINB, R::DEPTH>;
     }
-    cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S::SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                (int)cudaSharedmemCarveoutMaxShared);
+    return allow_smem(*fn, S::SMEM, true);
   } else {
     *fn = dev::tile_kernel<K, S::NT, S::IPT, false>;
     return cudaSuccess;
@@ -113,7 +136,7 @@ cudaError_t small_kernel_of(int nt, int cutoff, void (**fn)(SortParams), size_t 
       : nt == 512  ? dev::small_kernel<K, 512>
                    : dev::small_kernel<K, dev::kSmallThreads>;
   *smem = dev::small_smem_bytes<K>(cutoff, small_threads_of(nt));
-  return cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  return allow_smem(*fn, *smem, false);
 }
 
 template <typename K>
@@ -203,7 +226,7 @@ cudaError_t fused_kernel_of(int cutoff, void (**fn)(SortParams), size_t *smem) {
   static_assert(S::FORM == 0 && S::NT == 256, "fused shape");
   *fn = dev::tile_kernel<K, S::NT, S::IPT, true>;
   *smem = dev::fuse_smem_bytes<K>(cutoff, S::NT);
-  return cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  return allow_smem(*fn, *smem, false);
 }
 
 template <typename K>
@@ -229,10 +252,7 @@ template <typename K, typename S>
 cudaError_t part_kernel_of(void (**fn)(SortParams), size_t *smem) {
   *fn = dev::part_kernel<K, S::NT, S::IPT>;
   *smem = dev::pipe_smem_bytes<K, S::NT * S::IPT>();
-  cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared);
+  return allow_smem(*fn, *smem, true);
 }
 
 template <typename K>
@@ -304,11 +324,7 @@ decltype(auto) with_ring(int c, F &&f) {
 template <typename K, typename C>
 cudaError_t ring_kernel_of(void (**fn)(SortParams)) {
   *fn = dev::part_ring_kernel<K, C::NDW, C::IPT, C::S, C::MINB, C::PER, C::NLB, C::DEPTH, C::RESV>;
-  cudaError_t e = cudaFuncSetAttribute(*fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(*fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                              (int)cudaSharedmemCarveoutMaxShared);
+  return allow_smem(*fn, C::SMEM, true);
 }
 
 template <typename K>

@@ -119,17 +119,19 @@ struct SortStop {
 // after limit_ns, 2 once the CTA or the call stops, 3 once ring index `i` reaches
 // *end_at (when end_at is given: the tile will never come). Every lane takes the barrier
 // itself (so its later reads see what the arriving threads wrote) with the potentially
-// blocking try_wait without a time hint: the hardware suspends the thread until the
-// phase completes or, by its definition, a system-dependent time limit passes, so the
-// checks run on every return and no wait depends on a hint being honoured. The decision
-// to leave is lane 0's, broadcast, so the warp never splits.
+// blocking try_wait and a suspend-time hint of kRingSleepNs: the hardware suspends the
+// thread until the phase completes or about that time passes, so a waiting warp takes
+// almost no issue slots from the working ones. The checks run on every return, so no
+// wait depends on the hint being honoured; a stop is seen within a few hints. The
+// decision to leave is lane 0's, broadcast, so the warp never splits.
+constexpr unsigned kRingSleepNs = 20000;
 template <typename Stop>
 __device__ __forceinline__ int ring_wait_warp(unsigned long long *bar, unsigned parity,
                                               unsigned long long limit_ns, const Stop &st,
                                               const volatile int *end_at = nullptr, int i = 0) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
-    if (__all_sync(kFull, mbar_try_wait(bar, parity))) return 0;
+    if (__all_sync(kFull, mbar_try_wait_sleep(bar, parity, kRingSleepNs))) return 0;
     int r = 0;
     if ((threadIdx.x & 31) == 0) {
       if (end_at && i >= *end_at) r = 3;
@@ -152,7 +154,7 @@ __device__ __forceinline__ int ring_wait_one(unsigned long long *bar, unsigned p
                                              unsigned long long limit_ns, const Stop &st) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
-    if (mbar_try_wait(bar, parity)) return 0;
+    if (mbar_try_wait_sleep(bar, parity, kRingSleepNs)) return 0;
     if (*st.cta) return 2;
     if ((k & 7u) == 7u) {
       const unsigned long long now = globaltimer();
@@ -278,9 +280,10 @@ __device__ __forceinline__ void ring_compact(K *reg, K key, int a, int b, unsign
 // and ring_abort.
 // Tiles are anchored at the 16-byte boundary at or below element 1 (tile_base), so
 // every bulk copy starts aligned; it covers whole 16-byte chunks of the array.
-// (A fixed first tile per CTA would save the first claim, but then a CTA's later tiles
-// would wait for the first tiles of CTAs with higher indices, which another kernel on
-// the GPU can keep from starting.)
+// (In the ordered form, fixed first tiles would save claims, but then a CTA's later
+// tiles would wait for the first tiles of CTAs with higher indices, which another kernel
+// on the GPU can keep from starting; the reservation forms have no such wait and take
+// their first DEPTH tiles fixed.)
 template <typename K, int NDW, int IPT, int S, int MINB, int PER, int NLB, int DEPTH_,
           bool RESV = false>
 __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(SortParams p) {
@@ -307,11 +310,14 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
   const RingStop stp{stop, &ctl->ring_abort, epoch};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const K key = __ldcg(src);  // Step 1: the first element is the key
-  // First tile: in the reservation forms no tile waits for another, so CTA b takes
-  // tile b without a claim (later claims count from gridDim.x); the ordered form's tiles
-  // wait for their predecessors, so there every tile is claimed, in the order CTAs run.
+  // First tiles: in the reservation forms no tile waits for another, so CTA b takes
+  // tiles b, b + G, ..., b + (DEPTH - 1) G (G CTAs) without a claim, and its first DEPTH
+  // copies leave at once instead of one per claim's round trip; later claims count from
+  // DEPTH G. The ordered form's tiles wait for their predecessors, so there every tile
+  // is claimed, in the order CTAs run.
   constexpr bool kStaticFirst = NLB == 0 || RESV;
-  const unsigned long long t_first = kStaticFirst ? (unsigned long long)gridDim.x : 0ull;
+  const unsigned long long t_first =
+      kStaticFirst ? (unsigned long long)DEPTH * gridDim.x : 0ull;
   unsigned long long tk = 0;
   if (threadIdx.x == 0)
     tk = kStaticFirst ? (unsigned long long)blockIdx.x : atomicAdd(&ctl->part_ticket, 1ull);
@@ -365,6 +371,16 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
           sh.tix[i % R] = -1;
           *reinterpret_cast<volatile int *>(&sh.end_at) = i;
           mbar_arrive(&sh.full[s]);
+          if constexpr (NLB == 2) {
+            // The other role warp may already sleep on index i + 1, which never gets a
+            // tile: complete that phase of its barrier with no tile in it. The phase is
+            // the one for i + 1, since index i + 1 - S was counted before the DEPTH wait
+            // above let index i go; its tile-index entry was last read for index i - S,
+            // whose slot the empty wait above saw written out.
+            static_assert(NLB != 2 || (DEPTH < S && R == S + 1), "role-warp wake at the end");
+            sh.tix[(i + 1) % R] = -1;
+            mbar_arrive_n(&sh.counted[(i + 1) % S], (unsigned)NDW);
+          }
           break;
         }
         const long long t = (long long)tk;
@@ -378,7 +394,10 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
         if (p.trace && (unsigned long long)t < (unsigned long long)p.trace_cap)
           p.trace[t * kTraceWords + 7] = blockIdx.x | ((unsigned long long)i << 20) |
                                          ((unsigned long long)epoch << 40);
-        tk = t_first + atomicAdd(&ctl->part_ticket, 1ull);  // the next claim overlaps this copy
+        if (kStaticFirst && i + 1 < DEPTH)
+          tk = (unsigned long long)blockIdx.x + (unsigned long long)(i + 1) * gridDim.x;
+        else
+          tk = t_first + atomicAdd(&ctl->part_ticket, 1ull);  // the next claim overlaps this copy
       }
     }
     __syncwarp();
@@ -547,7 +566,9 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
       copy_out_v<K, 32>(reg + WT - G, dst + sh.gbase[s][dw], G, lane);
       fence_proxy_async_smem();  // the slot's next keys arrive by a bulk copy
       __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.empty[s]);
+      // the slot's reads fed the stores above, so they are done; the global stores need
+      // no ordering before the next copy into the slot
+      if (lane == 0) mbar_arrive_relaxed(&sh.empty[s]);
     };
     int wnext = 0;  // next of the CTA's tiles this warp writes out
     int i = 0;
@@ -590,7 +611,9 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
       __syncwarp();
       if (lane == 0) {
         sh.cnt[s][dw] = ((L + G) << 16) | L;
-        __threadfence_block();  // the counts before the tile's completion count
+        // the counts before the tile's completion count (the reservation forms publish
+        // them by the arrival on `counted`, which orders them itself)
+        if constexpr (!RESV) __threadfence_block();
         const unsigned old = RESV ? 0u : atomicAdd(&sh.acc[s], (1u << 20) + L);
         if (!RESV && (old >> 20) == (unsigned)NDW - 1u) {  // the last warp of the tile
           __threadfence_block();
