@@ -862,10 +862,13 @@ def run_serving(ks, count: int, tuning: dict | None):
     from paper_1107_3622_gb300 import autotune, serving
     # serving batches take the autotuner's choice for a batch of the size the server forms
     # at this load (about eight requests): eight arrays at the mix's octile sizes,
-    # 10^(3 + 4 (i + 1/2) / 8) keys (`tuning`, when given, is applied instead)
+    # 10^(3 + 4 (i + 1/2) / 8) keys, among the queue forms (tile shapes 1-9). The wave
+    # form's level-synchronous launches pay off on large batches only: under it the
+    # server sustained about half of its burst rate (`tuning`, when given, is applied
+    # instead)
     if tuning is None:
         lens = np.array([round(10 ** (3 + 4 * (i + 0.5) / 8)) for i in range(8)], np.int64)
-        e = autotune.autotune("batched", ks.F32, lengths=lens, reps=5)
+        e = autotune.autotune("batched", ks.F32, lengths=lens, reps=5, shapes=tuple(range(1, 10)))
         tuning = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, cached=e["cached"])
     for code in (ks.F32, ks.U32):
         ks.ksort_set_tuning(code, cutoff=tuning["cutoff"], ctas_per_sm=tuning["ctas_per_sm"] or -1,

@@ -100,13 +100,19 @@ def _store(key: str, entry: dict):
         os.replace(tmp, path)
 
 
-def _full_key(kind, dtype, n, lengths) -> str:
-    return f"{device_key()}|{library_hash()}|{workload_key(kind, dtype, n, lengths)}"
+def shapes_suffix(shapes) -> str:
+    """Cache-key suffix of a search limited to some tile shapes ('' when unlimited)."""
+    return f"|shapes={','.join(str(x) for x in shapes)}" if shapes else ""
 
 
-def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None) -> dict | None:
+def _full_key(kind, dtype, n, lengths, shapes=None) -> str:
+    k = f"{device_key()}|{library_hash()}|{workload_key(kind, dtype, n, lengths)}"
+    return k + shapes_suffix(shapes)
+
+
+def apply_cached(kind: str, dtype: int, n: int = 0, lengths=None, shapes=None) -> dict | None:
     """Applies a cached choice for this workload; returns it, or None if none is cached."""
-    e = _load_cache().get(_full_key(kind, dtype, n, lengths))
+    e = _load_cache().get(_full_key(kind, dtype, n, lengths, shapes))
     if not e:
         return None
     t = e["tuning"]
@@ -191,13 +197,17 @@ class _Runner:
 
 
 def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
-             seed: int | None = None, use_cache: bool = True, max_rounds: int = 2) -> dict:
-    """Searches and applies the best tuning for one workload; returns the cache entry."""
+             seed: int | None = None, use_cache: bool = True, max_rounds: int = 2,
+             shapes=None) -> dict:
+    """Searches and applies the best tuning for one workload; returns the cache entry.
+    `shapes` limits the tile shapes searched (default: all)."""
     import ksort_inputs as gen
     if kind not in ("sort", "batched", "partition"):
         raise ValueError("kind is 'sort', 'partition' or 'batched'")
+    if shapes is not None and not set(shapes) <= set(SHAPES):
+        raise ValueError("unknown tile shape")
     if use_cache:
-        e = apply_cached(kind, dtype, n, lengths)
+        e = apply_cached(kind, dtype, n, lengths, shapes)
         if e is not None:
             return dict(e, cached=True)
     if seed is None:
@@ -213,6 +223,8 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
             "finish_in_tiles": before.get("finish_in_tiles", -1),
             "finisher_threads": before.get("finisher_threads", 256),
             "cluster_sort": before.get("cluster_sort", -1)}
+    if shapes and best["tile_shape"] not in shapes:
+        best["tile_shape"] = shapes[0]
     tried = {}
 
     def measure(cfg) -> float:
@@ -235,7 +247,7 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
 
     best_ms = measure(best)
     axes = (("cluster_sort", CLUSTER_SORT if kind == "sort" else (-1,)),
-            ("tile_shape", SHAPES), ("wave_levels", WAVE_LEVELS),
+            ("tile_shape", tuple(shapes) if shapes else SHAPES), ("wave_levels", WAVE_LEVELS),
             ("finish_in_tiles", FINISH_IN_TILES), ("cutoff", cutoffs),
             ("ctas_per_sm", FINISHER_CTAS), ("finisher_threads", FINISHER_THREADS))
     if kind == "partition":
@@ -281,7 +293,7 @@ def autotune(kind: str, dtype: int, n: int = 0, lengths=None, reps: int = 3,
                              "cluster_sort": k[7], "ms": round(v, 4)}
                             for k, v in sorted(tried.items())]}
     if use_cache:
-        _store(_full_key(kind, dtype, n, lengths), entry)
+        _store(_full_key(kind, dtype, n, lengths, shapes), entry)
     return dict(entry, cached=False)
 
 

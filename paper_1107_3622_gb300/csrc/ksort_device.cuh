@@ -350,7 +350,7 @@ __device__ __forceinline__ bool tile_dest(long long begin, long long end, long l
 // ----------------------------------------------------------------------------- smem
 // Shared-memory finisher for one small sub-array (m <= cutoff keys) staged in buffer A,
 // run by one CTA of 256, 512 or 1024 threads. Its warps apply Steps 1-6: first CTA-wide partitions
-// while a segment is larger than kBlockSegment keys, then one warp per segment (Steps
+// while a segment is larger than block_segment(NT) keys, then one warp per segment (Steps
 // 1-4 by ballots from one buffer into the other; Steps 5-6 depth first, the smaller
 // side queued for another warp), and sides of at most kLeaf keys become leaves that
 // are finished in registers, several per warp (warp_leaf_run). Every key that reaches
@@ -360,13 +360,20 @@ __device__ __forceinline__ bool tile_dest(long long begin, long long end, long l
 #endif
 constexpr int kLeaf = KSORT_LEAF;
 static_assert(kLeaf >= 2 && kLeaf <= 32, "a leaf fits one warp");
-// Queued segments are disjoint; those above kLeaf keys number at most cutoff / 17 (for
-// leaves of at least 16 keys), and the CTA-wide phase queues at most two leaves per
-// partition: 1024 slots suffice for cutoffs up to 16384 keys.
+// Queued segments are disjoint; those above kLeaf (or kMarkLeaf) keys number at most
+// cutoff / 17 (for leaves of at least 16 keys), and the CTA-wide phase queues at most
+// two leaves per partition: 1024 slots suffice for cutoffs up to 16384 keys.
 constexpr int kSmallQueue = 1024;
 constexpr int kMaxSmallCutoff = 16384;
-constexpr int kBlockSegment = 1024;
-constexpr int kBigStack = kMaxSmallCutoff / kBlockSegment + 2;
+// Segments above block_segment(NT) keys are partitioned by the whole CTA (a count pass,
+// a scan and a scatter pass, three barriers), smaller ones by one warp in a single pass.
+// A 256-thread CTA, which serves many items at once, gains from the warp form's single
+// pass (7e6 f32 keys, cutoff 4096: 1024 -> 4096 takes the finisher from 0.270 to 0.254
+// ms); the larger CTAs, chosen to finish a few items soon, keep their warps busy with
+// the CTA form above 1024 keys.
+constexpr int kBlockSegmentMin = 1024;
+__host__ __device__ constexpr int block_segment(int nt) { return nt == 256 ? 4096 : kBlockSegmentMin; }
+constexpr int kBigStack = kMaxSmallCutoff / kBlockSegmentMin + 2;
 
 struct SmallShared {
   unsigned ring[kSmallQueue];         // queued segments: start << 16 | n << 1 | parity
@@ -619,7 +626,7 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
   } else {
     // CTA-wide partitions while segments are large (the top levels of the item)
     if (tid == 0) {
-      if (m > kBlockSegment) q.big[q.nbig++] = seg_pack(0, m, 0);
+      if (m > block_segment(NT)) q.big[q.nbig++] = seg_pack(0, m, 0);
       else small_push(q, 0, m, 0);
     }
     bsync();
@@ -639,7 +646,7 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int cs = c ? s + L + 1 : s, cn = c ? n - L - 1 : L;
-          if (cn > kBlockSegment) q.big[q.nbig++] = seg_pack(cs, cn, cp);
+          if (cn > block_segment(NT)) q.big[q.nbig++] = seg_pack(cs, cn, cp);
           else if (cn >= 2) small_push(q, cs, cn, cp);
           else if (cn == 1 && cp) A[cs] = Y[cs];
         }
@@ -720,9 +727,10 @@ __device__ bool smem_ksort(K *A, K *B, unsigned *leaf_lists, K *__restrict__ out
 }
 
 // Largest final segment of the marked form (2 .. 32): its closed form costs one compare
-// per key of the segment, and segments above it are partitioned by a warp.
+// per key of the segment, and segments above it are partitioned by a warp (measured
+// best at 20 of 12, 16, 20, 24 and 32).
 #ifndef KSORT_MARK_LEAF
-#define KSORT_MARK_LEAF 16
+#define KSORT_MARK_LEAF 20
 #endif
 constexpr int kMarkLeaf = KSORT_MARK_LEAF;
 static_assert(kMarkLeaf >= 2 && kMarkLeaf <= 32, "a marked segment spans at most two words");
@@ -772,7 +780,7 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
   if (tid == 0) {
     seg_mark(seg, m);
     if (m <= kMarkLeaf) mark_final(seg, par, 0, m, 0);
-    else if (m > kBlockSegment) q.big[q.nbig++] = seg_pack(0, m, 0);
+    else if (m > block_segment(NT)) q.big[q.nbig++] = seg_pack(0, m, 0);
     else small_push(q, 0, m, 0);
   }
   bsync();
@@ -794,7 +802,7 @@ __device__ bool smem_ksort_marked(K *A, K *B, unsigned *seg, unsigned *par,
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const int cs = c ? s + L + 1 : s, cn = c ? n - L - 1 : L;
-        if (cn > kBlockSegment) q.big[q.nbig++] = seg_pack(cs, cn, cp);
+        if (cn > block_segment(NT)) q.big[q.nbig++] = seg_pack(cs, cn, cp);
         else if (cn > kMarkLeaf) small_push(q, cs, cn, cp);
         else mark_final(seg, par, cs, cn, cp);
       }

@@ -207,6 +207,13 @@ def test_autotune_workload_keys():
     k = autotune.workload_key("batched", 2, lengths=np.array([100, 1000, 500_000]))
     assert k == "batched:u32:3x[100,500000]:2^19"
     assert len(autotune.library_hash()) == 16
+    # a search limited to some tile shapes is cached under its own key; unknown shapes
+    # are refused before any device work
+    assert autotune.shapes_suffix(None) == ""
+    assert autotune.shapes_suffix((1, 2, 3)) == "|shapes=1,2,3"
+    import pytest
+    with pytest.raises(ValueError):
+        autotune.autotune("batched", 2, lengths=np.array([100, 1000]), shapes=(0, 13))
 
 
 def _header_structs():

@@ -159,6 +159,23 @@ def test_autotuner_searches_applies_and_caches(ks, restore, tmp_path, monkeypatc
     assert eb["workload"].startswith("batched:f32:128x")
 
 
+def test_autotuner_limited_shapes(ks, restore, tmp_path, monkeypatch):
+    """A search limited to some tile shapes measures and picks only those, and caches
+    its choice apart from an unlimited search of the same workload."""
+    from paper_1107_3622_gb300 import autotune
+    monkeypatch.setenv("KSORT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    lengths = np.array([round(10 ** (3 + 4 * (i + 0.5) / 8)) for i in range(8)], np.int64)
+    ks.ksort_set_tuning(ks.F32, tile_shape=12)  # the incumbent lies outside the limit
+    e = autotune.autotune("batched", ks.F32, lengths=lengths, reps=2, max_rounds=1,
+                          shapes=(1, 2, 3))
+    assert {c["tile_shape"] for c in e["candidates"]} <= {1, 2, 3}
+    assert e["tuning"]["tile_shape"] in (1, 2, 3)
+    assert ks.ksort_get_tuning(ks.F32)["tile_shape"] == e["tuning"]["tile_shape"]
+    again = autotune.autotune("batched", ks.F32, lengths=lengths, shapes=(1, 2, 3))
+    assert again["cached"] and again["tuning"] == e["tuning"]
+    assert autotune.apply_cached("batched", ks.F32, lengths=lengths) is None
+
+
 def test_autotuner_partition_kind(ks, restore, tmp_path, monkeypatch):
     from paper_1107_3622_gb300 import autotune
     monkeypatch.setenv("KSORT_TUNE_CACHE", str(tmp_path / "tune.json"))
