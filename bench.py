@@ -324,10 +324,11 @@ def tile_kernel_name(ks, dtype_code: int) -> str:
     return f"{TILE_KERNELS[ks.ksort_tile_shape(dtype_code, shape)[2]]}/{shape}"
 
 
-def recorded_traffic(kernel: str, workload: str, part: str = ""):
+def recorded_traffic(kernel: str, workload: str, part: str = "", config: dict | None = None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel sources (else None): the whole call's, or with `part` that of the one
-    kernel whose name starts with it."""
+    current kernel sources and, when the entry names its tuning, under the tuning in
+    `config` (else None): the whole call's, or with `part` that of the one kernel whose
+    name starts with it."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -335,7 +336,9 @@ def recorded_traffic(kernel: str, workload: str, part: str = ""):
     except Exception:
         return None
     for r in rec.get("entries", []):
-        if r.get("kernel") == kernel and r.get("workload") == workload and \
+        rc = r.get("config")
+        same_config = rc is None or config is None or all(config.get(k) == v for k, v in rc.items())
+        if r.get("kernel") == kernel and r.get("workload") == workload and same_config and \
                 r.get("source_hash") == device_source_hash():
             if not part:
                 return r.get("dram_bytes_per_launch")
@@ -506,7 +509,7 @@ def run_ours(args, dist: Dist):
         if "batched" in extras:
             line["batched"] = run_batched(ks, args, peak, peak_src)
         if "serving" in extras and args.serving_requests > 0:
-            line["serving"] = run_serving(ks, args.serving_requests, None)
+            line["serving"] = run_serving(ks, args.serving_requests, tuning)
         if "cpu" in extras:
             v, sample, spent = cpu_baseline(min(n, N_KEYS), args.cpu_seconds, None)
             line["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1,
@@ -533,8 +536,10 @@ def sort_roofline(ks, stats, phases, ms_mean, n, peak, peak_src):
 
     # with finish_in_tiles the tile kernel also finishes some small sub-arrays; only the
     # tile passes' bytes are counted for it (a lower bound on its work)
+    cur = ks.ksort_get_tuning(ks.F32)
     fused_note = (", and some small sub-arrays (their bytes not counted here)"
-                  if ks.ksort_get_tuning(ks.F32).get("finish_in_tiles", -1) > 0 else "")
+                  if cur.get("finish_in_tiles", -1) > 0 else "")
+    cfg = {k: cur.get(k) for k in ("tile_shape", "cutoff", "finisher_threads")}
 
     parts = {
         "partition_passes": (f"{tk} <float>: the tile passes of every sub-array above the "
@@ -551,7 +556,7 @@ def sort_roofline(ks, stats, phases, ms_mean, n, peak, peak_src):
     ogbs, ofrac = entry(ob, oms)
     return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": frac,
             "peak_source": f"{peak_src} hbm_gbs",
-            "traffic": recorded_traffic(rec, WORKLOAD, prefix),
+            "traffic": recorded_traffic(rec, WORKLOAD, prefix, cfg),
             "kernel": name,
             "algorithmic_bytes_per_launch": bytes_,
             "launch_ms": round(ms, 4),
@@ -561,10 +566,10 @@ def sort_roofline(ks, stats, phases, ms_mean, n, peak, peak_src):
                           "finisher": round(mean[2], 4)},
             other: {"achieved": ogbs, "frac": ofrac, "algorithmic_bytes_per_launch": ob,
                     "launch_ms": round(oms, 4),
-                    "traffic": recorded_traffic(rec, WORKLOAD, parts[other][3])},
+                    "traffic": recorded_traffic(rec, WORKLOAD, parts[other][3], cfg)},
             "whole_call": {"achieved": round(call_gbs, 1), "frac": round(call_gbs / peak, 4),
                            "algorithmic_bytes_per_call": call_bytes,
-                           "traffic": recorded_traffic(rec, WORKLOAD),
+                           "traffic": recorded_traffic(rec, WORKLOAD, config=cfg),
                            "kernels": f"seed_kernel + {tk} + small_kernel, one ksort_sort call"},
             "lower_bound_bytes": 2 * 4 * n,
             "lower_bound_frac": round((2 * 4 * n) / (ms_mean / 1e3) / 1e9 / peak, 5)}
@@ -822,6 +827,8 @@ def run_batched(ks, args, peak, peak_src):
     algo = 2 * 4 * (stats["large_keys"] + stats["small_keys"])
     gbs = algo / (t_batched / 1e3) / 1e9
     rec = f"ksort_sort_batched<float> {tile_kernel_name(ks, ks.F32)}"
+    bt = ks.ksort_get_tuning(ks.F32)
+    bcfg = {k: bt.get(k) for k in ("tile_shape", "cutoff")}
     # restore the single-array tuning for what follows
     ks.ksort_set_tuning(ks.F32, cutoff=sort_tuning["cutoff"],
                         ctas_per_sm=sort_tuning["ctas_per_sm"] or -1,
@@ -845,38 +852,46 @@ def run_batched(ks, args, peak, peak_src):
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(gbs / peak, 4), "peak_source": f"{peak_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": algo,
-                         "traffic": recorded_traffic(rec, "4096-array batch, graph replay"),
+                         "traffic": recorded_traffic(rec, "4096-array batch, graph replay",
+                                                     config=bcfg),
                          "kernels": "the whole graph replay: seed, wave levels or tile passes, "
                                     "finisher"},
             "sort_stats": stats,
             "batched_tuning": batched_tuning, "loop_tuning": loop_tuning}
 
 
-def run_serving(ks, count: int, tuning: dict | None):
+def run_serving(ks, count: int, tuning: dict):
     """Serving configuration: `count` Poisson requests, sizes log-uniform in
     [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys in page-locked host memory,
     copied into an HBM arena at admission and back when sorted; the arena is sized from
     the HBM left free after the slot workspaces. The rate is 0.8 x the server's own
     throughput on a burst of 500 requests of the same mix, / mean keys per request."""
     import torch
-    from paper_1107_3622_gb300 import autotune, serving
-    # serving batches take the autotuner's choice for a batch of the size the server forms
-    # at this load (about eight requests): eight arrays at the mix's octile sizes,
-    # 10^(3 + 4 (i + 1/2) / 8) keys, among the queue forms (tile shapes 1-9). The wave
-    # form's level-synchronous launches pay off on large batches only: under it the
-    # server sustained about half of its burst rate (`tuning`, when given, is applied
-    # instead)
-    if tuning is None:
-        lens = np.array([round(10 ** (3 + 4 * (i + 0.5) / 8)) for i in range(8)], np.int64)
-        e = autotune.autotune("batched", ks.F32, lengths=lens, reps=5, shapes=tuple(range(1, 10)))
-        tuning = dict(ks.ksort_get_tuning(ks.F32), autotuned=True, cached=e["cached"])
-    for code in (ks.F32, ks.U32):
-        ks.ksort_set_tuning(code, cutoff=tuning["cutoff"], ctas_per_sm=tuning["ctas_per_sm"] or -1,
-                            tile_shape=tuning["tile_shape"],
-                            wave_levels=tuning.get("wave_levels", -1),
-                            finish_in_tiles=tuning.get("finish_in_tiles", -1),
-                            finisher_threads=tuning.get("finisher_threads", 256),
-                            cluster_sort=-1)
+    from paper_1107_3622_gb300 import serving
+    # The server's tuning: of the queue forms' three CTA shapes (tile shapes 1-3, at the
+    # sort's cutoff and finisher), the one with the highest burst capacity of the server
+    # itself (500 requests arriving at once, copies and slot overlap included). Tunings
+    # searched on lone serving-like batches won those batches but sustained less with four
+    # slots overlapping (the wave form above all): the queue never drained at 0.8 of the
+    # burst rate.
+    def apply(t):
+        for code in (ks.F32, ks.U32):
+            ks.ksort_set_tuning(code, cutoff=t["cutoff"], ctas_per_sm=t["ctas_per_sm"] or -1,
+                                tile_shape=t["tile_shape"], wave_levels=-1, finish_in_tiles=-1,
+                                finisher_threads=t.get("finisher_threads", 256),
+                                cluster_sort=-1)
+
+    calibration = []
+    for shape in (1, 2, 3):
+        cand = dict(tuning, tile_shape=shape)
+        apply(cand)
+        torch.cuda.empty_cache()
+        probe = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
+        calibration.append((serving.burst_capacity(probe), cand))
+        probe.close()
+        del probe
+    best_burst, chosen = max(calibration, key=lambda x: x[0])
+    apply(chosen)
     cap = serving.measure_capacity()
     torch.cuda.empty_cache()
     srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
@@ -911,9 +926,11 @@ def run_serving(ks, count: int, tuning: dict | None):
                 "host_pool_bytes": pools.nbytes(),
                 "alone_vs_mix_identical": mismatches == 0, "checked": len(reqs),
                 "mismatches": mismatches, "check_s": round(time.perf_counter() - t0, 2),
-                "pool_gen_s": round(gen_s, 2), "tuning": {k: tuning.get(k) for k in
-                                                           ("cutoff", "ctas_per_sm", "tile_shape", "wave_levels",
-                                                            "finish_in_tiles", "finisher_threads", "cluster_sort")},
+                "pool_gen_s": round(gen_s, 2),
+                "tuning": {k: chosen.get(k) for k in ("cutoff", "ctas_per_sm", "tile_shape",
+                                                      "finisher_threads")},
+                "tuning_calibration": [{"tile_shape": c["tile_shape"],
+                                        "burst_keys_per_s": round(b, 1)} for b, c in calibration],
                 "latency": "arrival -> completion event of the request's batch, which follows "
                            "the batch's host-to-device copy, sort and device-to-host copy",
                 "admission": "FIFO batches into a first-fit HBM arena sized from free memory; "

@@ -77,3 +77,24 @@ def test_reference_arm_prints_once_under_two_ranks():
     assert line["unit"] == "keys/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_recorded_traffic_matches_sources_and_tuning(tmp_path, monkeypatch):
+    """A recorded DRAM figure is returned only for the kernel sources it was captured on
+    and, when its entry names a tuning, only under that tuning."""
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    entry = {"kernel": "k", "workload": "w", "source_hash": "h", "dram_bytes_per_launch": 7,
+             "parts": {"tile_kernel<a>": 5, "small_kernel<b>": 2},
+             "config": {"tile_shape": 3, "cutoff": 4096}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"entries": [entry]}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "device_source_hash", lambda: "h")
+    assert bench.recorded_traffic("k", "w") == 7
+    assert bench.recorded_traffic("k", "w", config={"tile_shape": 3, "cutoff": 4096}) == 7
+    assert bench.recorded_traffic("k", "w", "small_kernel<", {"tile_shape": 3, "cutoff": 4096}) == 2
+    assert bench.recorded_traffic("k", "w", config={"tile_shape": 3, "cutoff": 8192}) is None
+    assert bench.recorded_traffic("k", "other") is None
+    monkeypatch.setattr(bench, "device_source_hash", lambda: "changed")
+    assert bench.recorded_traffic("k", "w") is None
