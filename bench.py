@@ -882,7 +882,7 @@ def run_serving(ks, count: int, tuning: dict):
                                 cluster_sort=-1)
 
     calibration = []
-    for shape in (1, 2, 3):
+    for shape in (3, 1, 2, 3):  # the first pass only warms up (module loading, pools)
         cand = dict(tuning, tile_shape=shape)
         apply(cand)
         torch.cuda.empty_cache()
@@ -890,6 +890,7 @@ def run_serving(ks, count: int, tuning: dict):
         calibration.append((serving.burst_capacity(probe), cand))
         probe.close()
         del probe
+    calibration = calibration[1:]
     best_burst, chosen = max(calibration, key=lambda x: x[0])
     apply(chosen)
     cap = serving.measure_capacity()
