@@ -20,7 +20,7 @@ Also reported on the same line:
                  median of runs), with the batch's roofline and phase split
   serving        10,000 Poisson requests (log-uniform 1e3..1e7 keys, half float32, half
                  uint32) in page-locked host memory, served by continuous batching on a
-                 stream pool, admitted into an HBM arena sized from free memory, at 0.8 x
+                 stream pool, admitted into an HBM arena sized from free memory, at 0.7 x
                  the server's measured burst capacity: keys/s, p50/p99 latency from arrival
                  (copies included), HBM budget and peak bytes in use, and every result
                  checked equal to the same request sorted alone
@@ -864,7 +864,7 @@ def run_serving(ks, count: int, tuning: dict):
     """Serving configuration: `count` Poisson requests, sizes log-uniform in
     [1e3, 1e7], 50/50 float32 U[0,1] / uint32 uniform, keys in page-locked host memory,
     copied into an HBM arena at admission and back when sorted; the arena is sized from
-    the HBM left free after the slot workspaces. The rate is 0.8 x the server's own
+    the HBM left free after the slot workspaces. The rate is 0.7 x the server's own
     throughput on a burst of 500 requests of the same mix, / mean keys per request."""
     import torch
     from paper_1107_3622_gb300 import serving
@@ -897,7 +897,9 @@ def run_serving(ks, count: int, tuning: dict):
     torch.cuda.empty_cache()
     srv = serving.Server(slots=4, slot_keys=1 << 27, max_arrays=4096)
     burst = serving.burst_capacity(srv)
-    rate = 0.8 * burst / serving.mean_length()
+    # 0.7: the server sustains about 0.82 of its burst rate on the mix, so at 0.8 it runs
+    # at the knee, where p99 swung between 44 and 221 ms from run to run
+    rate = 0.7 * burst / serving.mean_length()
     reqs = serving.poisson_requests(count, rate)
     t0 = time.perf_counter()
     pools = serving.build_pools(reqs)
@@ -920,7 +922,7 @@ def run_serving(ks, count: int, tuning: dict):
                 "capacity_keys_per_s": round(burst, 1),
                 "capacity": "the server's own throughput on 500 requests of the mix arriving at "
                             "once (copies, admission and slot overlap included); the rate is "
-                            "0.8 x that / mean keys per request",
+                            "0.7 x that / mean keys per request",
                 "one_batch_with_copies_keys_per_s": round(cap["with_copies_keys_per_s"], 1),
                 "one_batch_sort_only_keys_per_s": round(cap["sort_keys_per_s"], 1),
                 "slots": 4, "slot_keys": 1 << 27,
