@@ -1,6 +1,7 @@
-"""Host-side multi-rank logic of bench.py on CPU: two gloo ranks (replicas, weak
-scaling) agree on the max of their step times and the sum of their keys, and the
-reference arm under two ranks prints one line from rank 0 only."""
+"""Host-side logic of bench.py on CPU: two gloo ranks (replicas, weak scaling) agree on
+the max of their step times and the sum of their keys, and the reference arm under two
+ranks prints one line from rank 0 only; recorded DRAM traffic applies only to the kernel
+sources and tuning it was captured under; the sort roofline's arithmetic."""
 import json
 import os
 import socket
@@ -98,3 +99,28 @@ def test_recorded_traffic_matches_sources_and_tuning(tmp_path, monkeypatch):
     assert bench.recorded_traffic("k", "other") is None
     monkeypatch.setattr(bench, "device_source_hash", lambda: "changed")
     assert bench.recorded_traffic("k", "w") is None
+
+
+def test_sort_roofline_arithmetic(monkeypatch):
+    """The sort roofline: the dominant kernel is the phase with the longer mean time; its
+    achieved rate is 2 * 4 B per key it moves over that time, and the fraction divides by
+    the given peak; the other phase and the whole call are reported beside it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_1107_3622_gb300 as ks
+    ks.load()
+    monkeypatch.setattr(bench, "recorded_traffic", lambda *a, **k: None)
+    stats = {"large_keys": 100_000_000, "small_keys": 7_000_000}
+    phases = [[0.01, 0.40, 0.25], [0.01, 0.42, 0.25], [0.02]]  # a short record is skipped
+    r = bench.sort_roofline(ks, stats, phases, 0.70, 7_000_000, 6000.0, "measured")
+    assert r["launch_ms"] == 0.41 and r["algorithmic_bytes_per_launch"] == 800_000_000
+    assert r["achieved"] == round(800e6 / 0.41e-3 / 1e9, 1)
+    assert r["frac"] == round(800e6 / 0.41e-3 / 1e9 / 6000.0, 4)
+    assert r["finisher"]["algorithmic_bytes_per_launch"] == 56_000_000
+    assert r["finisher"]["launch_ms"] == 0.25
+    assert r["whole_call"]["algorithmic_bytes_per_call"] == 856_000_000
+    assert r["whole_call"]["frac"] == round(856e6 / 0.70e-3 / 1e9 / 6000.0, 4)
+    assert r["timing"].startswith("library phase events") and "2 timed steps" in r["timing"]
+    # a finisher that takes longer becomes the dominant kernel
+    r2 = bench.sort_roofline(ks, stats, [[0.01, 0.1, 0.3]], 0.45, 7_000_000, 6000.0, "measured")
+    assert r2["kernel"].startswith("small_kernel") and "partition_passes" in r2
