@@ -68,6 +68,11 @@ DEVICE_SOURCES = ("paper_1107_3622_gb300/csrc/ksort_device.cuh",
                   "paper_1107_3622_gb300/csrc/ksort_tile_ring.cuh",
                   "paper_1107_3622_gb300/csrc/ksort_launch.cuh",
                   "paper_1107_3622_gb300/csrc/ksort_internal.h")
+# the files that the sort's kernels (seed, tile passes of shapes 1-3, wave form, finisher)
+# are compiled from; a recorded figure may name the files it depends on
+SORT_SOURCES = ("paper_1107_3622_gb300/csrc/ksort_device.cuh",
+                "paper_1107_3622_gb300/csrc/ksort_launch.cuh",
+                "paper_1107_3622_gb300/csrc/ksort_internal.h")
 
 
 def parse_args(argv=None):
@@ -306,9 +311,9 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def device_source_hash():
+def device_source_hash(files=DEVICE_SOURCES):
     h = hashlib.sha256()
-    for rel in DEVICE_SOURCES:
+    for rel in files:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -326,9 +331,9 @@ def tile_kernel_name(ks, dtype_code: int) -> str:
 
 def recorded_traffic(kernel: str, workload: str, part: str = "", config: dict | None = None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel sources and, when the entry names its tuning, under the tuning in
-    `config` (else None): the whole call's, or with `part` that of the one kernel whose
-    name starts with it."""
+    current kernel sources (the files the entry names, else all device sources) and,
+    when the entry names its tuning, under the tuning in `config` (else None): the whole
+    call's, or with `part` that of the one kernel whose name starts with it."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -338,8 +343,9 @@ def recorded_traffic(kernel: str, workload: str, part: str = "", config: dict | 
     for r in rec.get("entries", []):
         rc = r.get("config")
         same_config = rc is None or config is None or all(config.get(k) == v for k, v in rc.items())
+        files = tuple(r.get("sources") or DEVICE_SOURCES)
         if r.get("kernel") == kernel and r.get("workload") == workload and same_config and \
-                r.get("source_hash") == device_source_hash():
+                r.get("source_hash") == device_source_hash(files):
             if not part:
                 return r.get("dram_bytes_per_launch")
             hits = [v for k, v in r.get("parts", {}).items() if k.startswith(part)]

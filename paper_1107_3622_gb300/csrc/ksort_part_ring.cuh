@@ -119,11 +119,16 @@ struct SortStop {
 // after limit_ns, 2 once the CTA or the call stops, 3 once ring index `i` reaches
 // *end_at (when end_at is given: the tile will never come). Every lane takes the barrier
 // itself (so its later reads see what the arriving threads wrote) with the potentially
-// blocking try_wait and a suspend-time hint of kRingSleepNs: the hardware suspends the
-// thread until the phase completes or about that time passes, so a waiting warp takes
-// almost no issue slots from the working ones. The checks run on every return, so no
-// wait depends on the hint being honoured; a stop is seen within a few hints. The
-// decision to leave is lane 0's, broadcast, so the warp never splits.
+// blocking try_wait: the hardware suspends the thread until the phase completes or a
+// time limit passes, so a waiting warp takes almost no issue slots from the working
+// ones. Waits that only a phase completion ends take a suspend-time hint of
+// kRingSleepNs; waits that an end mark may end instead (end_at given) take none, since
+// the end mark arrives on no barrier and must be seen by polling. The checks run on every
+// return, so no wait depends on the hint being honoured; a stop is seen within a few
+// hints. The decision to leave is lane 0's, broadcast, so the warp never splits.
+// (Waking such a waiter by completing its barrier's phase at the end mark is not safe:
+// the arrival can complete the phase after the one that the same warp has yet to see,
+// and a parity wait cannot tell the two apart.)
 constexpr unsigned kRingSleepNs = 20000;
 template <typename Stop>
 __device__ __forceinline__ int ring_wait_warp(unsigned long long *bar, unsigned parity,
@@ -131,7 +136,9 @@ __device__ __forceinline__ int ring_wait_warp(unsigned long long *bar, unsigned 
                                               const volatile int *end_at = nullptr, int i = 0) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
-    if (__all_sync(kFull, mbar_try_wait_sleep(bar, parity, kRingSleepNs))) return 0;
+    const bool done = end_at ? mbar_try_wait(bar, parity)
+                             : mbar_try_wait_sleep(bar, parity, kRingSleepNs);
+    if (__all_sync(kFull, done)) return 0;
     int r = 0;
     if ((threadIdx.x & 31) == 0) {
       if (end_at && i >= *end_at) r = 3;
@@ -371,16 +378,6 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
           sh.tix[i % R] = -1;
           *reinterpret_cast<volatile int *>(&sh.end_at) = i;
           mbar_arrive(&sh.full[s]);
-          if constexpr (NLB == 2) {
-            // The other role warp may already sleep on index i + 1, which never gets a
-            // tile: complete that phase of its barrier with no tile in it. The phase is
-            // the one for i + 1, since index i + 1 - S was counted before the DEPTH wait
-            // above let index i go; its tile-index entry was last read for index i - S,
-            // whose slot the empty wait above saw written out.
-            static_assert(NLB != 2 || (DEPTH < S && R == S + 1), "role-warp wake at the end");
-            sh.tix[(i + 1) % R] = -1;
-            mbar_arrive_n(&sh.counted[(i + 1) % S], (unsigned)NDW);
-          }
           break;
         }
         const long long t = (long long)tk;
@@ -566,9 +563,7 @@ __global__ void __launch_bounds__((NDW + 1 + NLB) * 32, MINB) part_ring_kernel(S
       copy_out_v<K, 32>(reg + WT - G, dst + sh.gbase[s][dw], G, lane);
       fence_proxy_async_smem();  // the slot's next keys arrive by a bulk copy
       __syncwarp();
-      // the slot's reads fed the stores above, so they are done; the global stores need
-      // no ordering before the next copy into the slot
-      if (lane == 0) mbar_arrive_relaxed(&sh.empty[s]);
+      if (lane == 0) mbar_arrive(&sh.empty[s]);
     };
     int wnext = 0;  // next of the CTA's tiles this warp writes out
     int i = 0;

@@ -91,13 +91,13 @@ def test_recorded_traffic_matches_sources_and_tuning(tmp_path, monkeypatch):
              "config": {"tile_shape": 3, "cutoff": 4096}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"entries": [entry]}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "device_source_hash", lambda: "h")
+    monkeypatch.setattr(bench, "device_source_hash", lambda *a: "h")
     assert bench.recorded_traffic("k", "w") == 7
     assert bench.recorded_traffic("k", "w", config={"tile_shape": 3, "cutoff": 4096}) == 7
     assert bench.recorded_traffic("k", "w", "small_kernel<", {"tile_shape": 3, "cutoff": 4096}) == 2
     assert bench.recorded_traffic("k", "w", config={"tile_shape": 3, "cutoff": 8192}) is None
     assert bench.recorded_traffic("k", "other") is None
-    monkeypatch.setattr(bench, "device_source_hash", lambda: "changed")
+    monkeypatch.setattr(bench, "device_source_hash", lambda *a: "changed")
     assert bench.recorded_traffic("k", "w") is None
 
 
@@ -124,3 +124,20 @@ def test_sort_roofline_arithmetic(monkeypatch):
     # a finisher that takes longer becomes the dominant kernel
     r2 = bench.sort_roofline(ks, stats, [[0.01, 0.1, 0.3]], 0.45, 7_000_000, 6000.0, "measured")
     assert r2["kernel"].startswith("small_kernel") and "partition_passes" in r2
+
+
+def test_recorded_traffic_checks_the_files_an_entry_names(tmp_path, monkeypatch):
+    """An entry that names its source files is checked against the hash of those files
+    alone, so a change elsewhere in the device sources leaves it valid."""
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    entries = [{"kernel": "k", "workload": "w", "sources": ["a.cuh"], "source_hash": "ha",
+                "dram_bytes_per_launch": 3},
+               {"kernel": "k2", "workload": "w", "source_hash": "ha", "dram_bytes_per_launch": 4}]
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"entries": entries}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "device_source_hash",
+                        lambda files=bench.DEVICE_SOURCES: "ha" if tuple(files) == ("a.cuh",) else "all")
+    assert bench.recorded_traffic("k", "w") == 3
+    assert bench.recorded_traffic("k2", "w") is None
